@@ -1,0 +1,249 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against facts fixed independently of it: values the
+paper prints (Table 1 totals, the Section 2.3 examples), textbook units of
+small real quadratic fields, brute-force solutions of x^2 - d y^2 = +-4
+(Lemma 1.1(ii)), class numbers counted as cycles of reduced forms
+(Lemma 1.1(iv)), a Moebius count of square-free d == 5 (mod 8), library
+routines (math.isqrt, sympy) and the asymptotic fit of Section 3.1.
+"""
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper():
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- helpers
+
+def mobius_upto(n):
+    mu = np.ones(n + 1, dtype=np.int64)
+    is_p = np.ones(n + 1, dtype=bool)
+    is_p[:2] = False
+    for p in range(2, n + 1):
+        if is_p[p]:
+            is_p[2 * p::p] = False
+            mu[p::p] *= -1
+            mu[p * p::p * p] = 0
+    return mu
+
+
+def count_D_mobius(lo, hi):
+    """#{d in [lo,hi): d == 5 mod 8, d square-free} by inclusion-exclusion:
+    sum over odd m of mu(m) * #{d in [lo,hi): d == 5 mod 8, m^2 | d}; the
+    inner condition is the single class d == 5 m^2 (mod 8 m^2) because
+    m^2 == 1 (mod 8) for odd m."""
+    M = math.isqrt(max(hi - 1, 0))
+    mu = mobius_upto(M + 1)
+    tot = 0
+    for m in range(1, M + 1, 2):
+        if mu[m] == 0:
+            continue
+        mod = 8 * m * m
+        r = 5 * m * m
+        cnt = (hi - 1 - r) // mod - (lo - 1 - r) // mod
+        tot += int(mu[m]) * cnt
+    return tot
+
+
+# ---------------------------------------------------------------- integers
+
+def test_isqrt_matches_math_isqrt(orc):
+    rng = random.Random(1)
+    vals = list(range(0, 5000)) + [rng.randrange(1 << 62) for _ in range(3000)]
+    vals += [k * k + e for k in (2**31 - 1, 10**6, 3037000499) for e in (-1, 0, 1)]
+    for n in vals:
+        if n < 0:
+            continue
+        assert orc.isqrt(n) == math.isqrt(n), n
+
+
+def test_squarefree_matches_factorisation(orc):
+    sympy = pytest.importorskip("sympy")
+    rng = random.Random(2)
+    vals = list(range(1, 3000)) + [rng.randrange(1, 10**12) for _ in range(400)]
+    for n in vals:
+        expect = all(e == 1 for e in sympy.factorint(n).values())
+        assert orc.is_squarefree(n) == expect, n
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 10**5), (5, 6), (0, 5), (12345, 67891),
+                                   (10**9, 10**9 + 3 * 10**5),
+                                   (10**12 - 10**5, 10**12 + 7)])
+def test_count_of_D_matches_moebius(orc, lo, hi):
+    flags, nD = orc.sqfree_range(lo, hi)
+    assert nD == count_D_mobius(lo, hi) == int(flags.sum())
+    if hi < 10**7:
+        codes = orc.classify_range(lo, hi)["codes"]
+        assert np.array_equal(codes > 0, flags > 0)
+
+
+def test_classify_codes_match_pointwise_definition(orc):
+    lo, hi = 999_000, 1_000_500
+    out = orc.classify_range(lo, hi)
+    d0 = out["d0"]
+    assert d0 % 8 == 5 and lo <= d0 < lo + 8
+    for k, code in enumerate(out["codes"]):
+        d = d0 + 8 * k
+        assert d < hi
+        assert (code > 0) == orc.in_D(d)
+        if code:
+            rc, theta, _ = orc.walk_mod2(d)
+            assert rc == 0 and (code == 2) == (theta == 1)
+
+
+# ---------------------------------------------------------------- units
+
+# Fundamental units of small fields, eps = (x0 + y0 sqrt d)/2 (textbook values,
+# e.g. the tables of fundamental units of real quadratic fields).
+TEXTBOOK_UNITS = {5: (1, 1, -1), 13: (3, 1, -1), 21: (5, 1, 1), 29: (5, 1, -1),
+                  37: (12, 2, -1), 53: (7, 1, -1), 61: (39, 5, -1), 69: (25, 3, 1),
+                  77: (9, 1, 1), 93: (29, 3, 1), 101: (20, 2, -1)}
+
+
+@pytest.mark.parametrize("d", sorted(TEXTBOOK_UNITS))
+def test_textbook_units(orc, d):
+    x0, y0, nrm = TEXTBOOK_UNITS[d]
+    u = orc.unit_exact(d)
+    assert (u["x0"], u["y0"], u["norm"]) == (x0, y0, nrm)
+    # Lemma 1.1(i) via O_K coordinates: eps = u + v*omega, u=(x0-y0)/2, v=y0
+    in_E = ((x0 - y0) // 2) % 2 == 1 and y0 % 2 == 0
+    assert u["flag"] == in_E
+    rc, theta, per = orc.walk_mod2(d)
+    assert rc == 0 and (theta == 1) == in_E and per == u["period"]
+
+
+def test_paper_examples_in_E(orc):
+    for d in paper()["examples_in_E"]["d"]:
+        assert orc.in_D(d)
+        assert orc.unit_exact(d)["flag"] is True
+        rc, theta, _ = orc.walk_mod2(d)
+        assert rc == 0 and theta == 1
+
+
+def test_small_cases_not_in_E(orc):
+    for d, theta in [(5, 2), (13, 3), (21, 2), (29, 2)]:
+        rc, th, _ = orc.walk_mod2(d)
+        assert rc == 0 and th == theta
+
+
+def test_not_in_D_rejected(orc):
+    for d in [1, 3, 4, 9, 45, 125, 9 * 13 * 13 * 8 + 0, 6]:
+        if d % 8 == 5 and orc.is_squarefree(d):
+            continue
+        assert orc.walk_mod2(d)[0] == orc.ORC_ENOTD
+
+
+def test_unit_is_fundamental_by_brute_force(orc):
+    """Lemma 1.1(ii) side: the least y >= 1 solving x^2 - d y^2 = +-4 gives the
+    fundamental unit; compare with Oracle-A for every d in D below 2000 whose
+    y0 is within the search bound, and with sympy's Pell solver otherwise."""
+    ymax = 100_000
+    checked_brute, rest = 0, []
+    for d in range(5, 2000, 8):
+        if not orc.in_D(d):
+            continue
+        u = orc.unit_exact(d)
+        if u["y0"] is not None and u["y0"] <= ymax:
+            y, x, sg = orc.pell_smallest(d, u["y0"])
+            assert (y, x, sg) == (u["y0"], u["x0"], u["norm"]), d
+            assert orc.pell_smallest(d, u["y0"] - 1) is None if u["y0"] > 1 else True
+            checked_brute += 1
+        else:
+            rest.append(d)
+    assert checked_brute > 150
+    sympy = pytest.importorskip("sympy")
+    from sympy.solvers.diophantine.diophantine import diop_DN
+    for d in rest:
+        sols = [s for N in (4, -4) for s in diop_DN(d, N) if s[1] > 0]
+        y = min(s[1] for s in sols)
+        u = orc.unit_exact(d)
+        assert u["y0_bits"] == int(y).bit_length(), d
+        assert u["y0_parity"] == int(y) % 2, d
+
+
+def test_oracle_A_and_B_agree(orc):
+    """Exact unit (Oracle-A) and the mod-2 walk (Oracle-B) agree on every d in D
+    below 10^5 on the class of eps_d mod 2O_K and on the period."""
+    n = 0
+    for d in range(5, 100_000, 8):
+        if not orc.in_D(d):
+            continue
+        u = orc.unit_exact(d)
+        rc, theta, per = orc.walk_mod2(d)
+        assert rc == 0
+        assert theta == u["theta"] and per == u["period"], d
+        n += 1
+    assert n > 10_000
+
+
+def test_lemma_1_1_iv_class_numbers(orc):
+    """h+(4d) = 3 h+(d) iff d in E, else h+(4d) = h+(d) (Lemma 1.1(iv); the
+    index [O_K*: Z[sqrt d]*] is 1 or 3 for totally positive units too)."""
+    seen_E = seen_not = 0
+    for d in range(5, 20_000, 8):
+        if not orc.in_D(d):
+            continue
+        h1 = orc.narrow_classno(d)
+        h4 = orc.narrow_classno(4 * d)
+        rc, theta, _ = orc.walk_mod2(d)
+        assert rc == 0
+        if theta == 1:
+            assert h4 == 3 * h1, d
+            seen_E += 1
+        else:
+            assert h4 == h1, d
+            seen_not += 1
+    assert seen_E > 300 and seen_not > 600
+
+
+def test_lemma_1_1_ii_odd_solutions(orc):
+    """d in E iff x^2 - d y^2 = 4 has no solution in odd x, y (Lemma 1.1(ii)).
+    For d not in E a solution with y <= y0 * x0 exists (eps or eps^2); search
+    it directly; for d in E no odd solution may appear below the bound."""
+    for d in range(5, 700, 8):
+        if not orc.in_D(d):
+            continue
+        u = orc.unit_exact(d)
+        bound = min(u["x0"] * u["y0"], 200_000)
+        found = False
+        for y in range(1, bound + 1, 2):
+            v = d * y * y + 4
+            x = math.isqrt(v)
+            if x * x == v and x % 2 == 1:
+                found = True
+                break
+        if u["flag"]:
+            assert not found, d
+        elif u["x0"] * u["y0"] <= 200_000:
+            assert found, d
+
+
+def test_fit_at_1e6(orc):
+    """pi_E(10^6) lies within 2% of x/(3 pi^2) - 0.024 x^(5/6) (Section 3.1)."""
+    x = 10**6
+    nD, nE, _ = orc.count_range(0, x + 1)
+    fit = x / (3 * math.pi**2) - 0.024 * x ** (5 / 6)
+    assert abs(nE - fit) / fit < 0.02
+    # pi_D(x) = x/pi^2 + O(x^(1/2+eps)) (Section 1)
+    assert abs(nD - x / math.pi**2) < 3 * math.sqrt(x)
+    assert nD == count_D_mobius(0, x + 1)
+
+
+@pytest.mark.slow
+def test_table1_pi_E_1e8(orc):
+    """Table 1: #E cap [0, 10^8] = 3 259 668 (sum of the h* rows)."""
+    iv = paper()["table1_totals"]["intervals"][0]
+    assert (iv["lo"], iv["hi"]) == (0, 10**8)
+    nD, nE, _ = orc.count_range(0, 10**8 + 1)
+    assert nE == iv["total"]
+    assert nD == count_D_mobius(0, 10**8 + 1)
