@@ -1,0 +1,196 @@
+/*
+ * eis.h -- C-ABI of the GB300 (sm_103a) Eisenstein-discriminant library.
+ *
+ * What it computes (Breuer & Punch, "Quadratic units and cubic fields"):
+ *   D  = { d > 0 : d == 5 (mod 8), d square-free }              (Section 1)
+ *   E  = { d in D : eps_d == 1 (mod 2O_K) }, eps_d the fundamental unit of
+ *        K = Q(sqrt d), O_K = Z[(1+sqrt d)/2]                     (Section 1)
+ *   pi_E(x) = #{ d in E : d <= x }                                (Section 1)
+ * eps_d mod 2O_K is found by the infrastructure baby steps of Appendix A
+ * with every generator reduced into (O_K/2O_K)* = F_4* = Z/3 (Appendix A,
+ * last paragraphs before the implementation notes).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Ranges are half-open [lo, hi); pi_E(x) = count over [0, x+1).  Supported
+ * values: hi <= EIS_D_LIMIT (2^44); larger give EIS_ERANGE.
+ *
+ * Candidates: the d == 5 (mod 8) in [lo, hi), d = d0 + 8k, k = 0..n-1, with
+ * d0 the least such d >= lo.  Bit-packed outputs use 32-bit words, bit
+ * (k & 31) of word (k >> 5), little-endian bit order; unused high bits of
+ * the last word are 0.  Flag bit = [d in E]; square-free bit = [d in D];
+ * a candidate that is not square-free has flag 0.
+ *
+ * Ownership: the caller owns every output buffer; the context owns its
+ * device memory (prime table, bitmaps, work queues), streams and graphs.
+ * A context is not thread-safe: one host thread uses it at a time.
+ *
+ * Errors: every function returns EIS_OK (0) or a negative EIS_E* code and
+ * then writes no output.  eis_strerror() names a code.  Device memory is
+ * allocated only in eis_create / eis_plan_create / the convenience calls
+ * (which size their work to the context's memory budget), never inside
+ * eis_plan_launch.
+ */
+#ifndef EIS_GB300_H
+#define EIS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EIS_OK 0
+#define EIS_EINVAL -1    /* null pointer where one is required, lo > hi, bad option */
+#define EIS_ENOTD -2     /* is_eisenstein: d is not in D (no result written) */
+#define EIS_ERANGE -3    /* hi (or d) above EIS_D_LIMIT */
+#define EIS_ENOMEM -4    /* device or host allocation failed / over budget */
+#define EIS_ETIMEOUT -5  /* a wait for a result ran past its limit */
+#define EIS_EDEVICE -6   /* a CUDA call failed; the context should be destroyed */
+#define EIS_ESTEPS -7    /* a walk ran past its step limit (never expected) */
+#define EIS_EBUSY -8     /* serving: request not admitted (queue or memory full) */
+#define EIS_ENOTFOUND -9 /* serving: unknown request id */
+
+/* Exclusive upper bound on hi (and on d): 2^44.  Below it every baby-step
+ * quantity (P, Q, P + floor(sqrt d)) is an integer below 2^23, which the
+ * kernels carry exactly in fp32 registers. */
+#define EIS_D_LIMIT (((uint64_t)1) << 44)
+
+/* Execution modes (eis_set_option(EIS_OPT_MODE)). */
+#define EIS_MODE_PLAIN 0      /* one launch per 2^24-wide block of d, one    */
+                              /* thread per candidate                         */
+#define EIS_MODE_PERSISTENT 1 /* sieve + compaction + one persistent launch   */
+                              /* whose lanes steal d's from a global queue   */
+                              /* (CUDA-graph captured per plan)               */
+
+/* Options (eis_set_option / eis_get_option). */
+#define EIS_OPT_MODE 1           /* EIS_MODE_*; default EIS_MODE_PERSISTENT   */
+#define EIS_OPT_CTAS_PER_SM 2    /* persistent grid: CTAs per SM (default 0 = */
+                                 /* occupancy maximum)                        */
+#define EIS_OPT_THREADS 3        /* threads per CTA of the walk kernels (256) */
+#define EIS_OPT_STEP_LIMIT 4     /* per-d baby-step limit before EIS_ESTEPS   */
+#define EIS_OPT_USE_GRAPH 5      /* 1: capture plans into CUDA graphs (1)     */
+#define EIS_OPT_GIANT_THRESHOLD 6 /* baby steps after which a d is handed to  */
+                                  /* the giant-step kernel (0 = never)        */
+#define EIS_OPT_GIANT_STRIDE 7   /* giant-step stride in baby steps (0: auto) */
+
+typedef struct eis_ctx eis_ctx;
+typedef struct eis_plan eis_plan;
+
+/* Per-call statistics of the last plan launch / convenience call. */
+typedef struct {
+    uint64_t candidates;  /* d == 5 (mod 8) examined */
+    uint64_t in_D;        /* square-free candidates (#D) */
+    uint64_t in_E;        /* #E */
+    uint64_t baby_steps;  /* rho steps walked by the walk kernels */
+    uint64_t giant_steps; /* giant steps (compositions) */
+    uint64_t deferred;    /* d handed from the baby to the giant kernel */
+    double ms_total;      /* device time of the whole plan (CUDA events) */
+    double ms_walk;       /* device time of the walk kernel(s) */
+    double ms_sieve;      /* device time of sieve + compaction */
+    double ms_giant;      /* device time of the giant-step kernel */
+    int launches;         /* kernels launched by the plan */
+    int sm_count;
+} eis_stats;
+
+/* ---------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * device memory the context and its plans may hold (0: 3/4 of free memory).
+ * Builds the odd-prime table up to 2^22 (for the square-free sieve of d <
+ * 2^44) on the device.  *out receives the context. */
+int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes);
+
+/* Release every resource of the context (plans made from it must be
+ * destroyed first).  NULL is accepted. */
+int eis_destroy(eis_ctx *ctx);
+
+/* Static text for an EIS_* code. */
+const char *eis_strerror(int code);
+
+/* Text of the CUDA error behind the calling thread's last EIS_EDEVICE. */
+const char *eis_last_cuda_error_string(void);
+
+int eis_set_option(eis_ctx *ctx, int key, int64_t value);
+int eis_get_option(eis_ctx *ctx, int key, int64_t *value);
+
+/* Statistics of the most recent call on this context. */
+int eis_get_stats(eis_ctx *ctx, eis_stats *out);
+
+/* ---------------------------------------------------------------------
+ * Convenience calls (synchronous; allocate and free per call, chunked to
+ * the memory budget)
+ * ------------------------------------------------------------------- */
+
+/* *count_out = #E cap [lo, hi)   (pi_E(x) = count over [0, x+1), Section 1). */
+int eis_count_range(eis_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *count_out);
+
+/* Classify every candidate of [lo, hi).
+ *   flags_out  : ceil(n/32) words, bit = [d in E]            (nullable)
+ *   sqfree_out : ceil(n/32) words, bit = [d in D]            (nullable)
+ *   out_on_device : 1 if flags_out/sqfree_out are device pointers (written
+ *                   in stream order on `stream`), 0 for host memory
+ *   count_out  : #E cap [lo, hi)                             (nullable)
+ *   stream     : cudaStream_t to run on (NULL: the context's stream)
+ * Returns after the results are complete. */
+int eis_classify_range(eis_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *flags_out,
+                       uint32_t *sqfree_out, int out_on_device, uint64_t *count_out,
+                       void *stream);
+
+/* One byte per candidate: 0 = d not in D, 1 = d in D \ E, 2 = d in E. */
+int eis_classify_range_u8(eis_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *codes_out,
+                          int out_on_device, uint64_t *count_out, void *stream);
+
+/* One byte per candidate: 0 = d not in D, else 1 + log_omega(eps_d mod 2O_K)
+ * in F_4* = {1, omega, omega^2} (so 1 = d in E, 2 = eps_d == omega,
+ * 3 = eps_d == omega^2 = 1 + omega), eps_d the unit reached by walking the
+ * cycle forward from O_K (Appendix A: theta_{l+1}).  For the distribution
+ * of eps_d mod 2O_K over the three classes (Section 1's a-priori 1/3). */
+int eis_classify_range_log(eis_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *log_out,
+                           int out_on_device, void *stream);
+
+/* *result_out = 1 if d is in E, 0 if d is in D \ E (Section 1, Lemma 1.1(i)).
+ * d not in D: EIS_ENOTD and nothing written. */
+int eis_is_eisenstein(eis_ctx *ctx, uint64_t d, int *result_out);
+
+/* counts_out[i] = #E cap [lo[i], hi[i]) for i < n, all intervals classified
+ * in one plan (one persistent launch). */
+int eis_count_batch(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t n,
+                    uint64_t *counts_out);
+
+/* ---------------------------------------------------------------------
+ * Plans: device-resident, re-launchable pipelines over a fixed set of
+ * intervals (what the benchmark times).
+ * ------------------------------------------------------------------- */
+
+/* Build a plan for the n intervals [lo[i], hi[i]) in `mode`.  Allocates all
+ * device memory the pipeline needs (bitmaps, survivor queue, counters) and,
+ * if EIS_OPT_USE_GRAPH, captures the pipeline into a CUDA graph. */
+int eis_plan_create(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t n,
+                    int mode, eis_plan **out);
+
+/* Enqueue one full pass (sieve, walk, count) on `stream` (NULL: the
+ * context's stream).  Asynchronous; allocates nothing. */
+int eis_plan_launch(eis_plan *plan, void *stream);
+
+/* Wait for the last launch and copy the per-interval #E to counts_out[n]. */
+int eis_plan_counts(eis_plan *plan, uint64_t *counts_out);
+
+/* Device pointers to the plan's bitmaps (valid until eis_plan_destroy):
+ * flags/sqfree words for the concatenated candidates; interval i starts at
+ * word word_offset[i] (host array of n entries, written if non-NULL). */
+int eis_plan_bitmaps(eis_plan *plan, const uint32_t **flags, const uint32_t **sqfree,
+                     uint64_t *word_offset, uint64_t *total_words);
+
+/* Wait for the last launch and fill `out` (device times from CUDA events). */
+int eis_plan_stats(eis_plan *plan, eis_stats *out);
+
+int eis_plan_destroy(eis_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

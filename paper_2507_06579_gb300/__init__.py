@@ -1,0 +1,324 @@
+"""Eisenstein discriminants on GB300 (sm_103a): Python binding.
+
+Thin ctypes marshalling over the C-ABI of ``include/eis.h``; every step of
+the computation runs in the CUDA kernels of ``libeis_gb300.so`` (built
+in-tree by :func:`build`).  There is no CPU fallback: if the library is not
+built, or no GPU is present, the calls raise.
+
+The functions mirror the C entry points::
+
+    ctx = Context(device=0)
+    ctx.count_range(lo, hi)                  # eis_count_range
+    ctx.classify_range(lo, hi)               # eis_classify_range (bit-packed)
+    ctx.classify_range_u8(lo, hi)            # eis_classify_range_u8
+    ctx.classify_range_log(lo, hi)           # eis_classify_range_log
+    ctx.is_eisenstein(d)                     # eis_is_eisenstein
+    ctx.count_batch(los, his)                # eis_count_batch
+    plan = ctx.plan_create(los, his, mode)   # eis_plan_* (device-resident pipeline)
+
+Device outputs may be torch CUDA tensors (their ``data_ptr()`` is passed);
+streams may be ``torch.cuda.Stream`` objects.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+EIS_OK = 0
+EIS_EINVAL = -1
+EIS_ENOTD = -2
+EIS_ERANGE = -3
+EIS_ENOMEM = -4
+EIS_ETIMEOUT = -5
+EIS_EDEVICE = -6
+EIS_ESTEPS = -7
+EIS_EBUSY = -8
+EIS_ENOTFOUND = -9
+
+EIS_D_LIMIT = 1 << 44
+
+EIS_MODE_PLAIN = 0
+EIS_MODE_PERSISTENT = 1
+
+EIS_OPT_MODE = 1
+EIS_OPT_CTAS_PER_SM = 2
+EIS_OPT_THREADS = 3
+EIS_OPT_STEP_LIMIT = 4
+EIS_OPT_USE_GRAPH = 5
+EIS_OPT_GIANT_THRESHOLD = 6
+EIS_OPT_GIANT_STRIDE = 7
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EisError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().eis_strerror(code).decode()
+        if code == EIS_EDEVICE:
+            msg += " [%s]" % lib().eis_last_cuda_error_string().decode()
+        super().__init__("%s failed: %s (%d)" % (where, msg, code))
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_uint64), ("in_D", ctypes.c_uint64),
+                ("in_E", ctypes.c_uint64), ("baby_steps", ctypes.c_uint64),
+                ("giant_steps", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
+                ("ms_total", ctypes.c_double), ("ms_walk", ctypes.c_double),
+                ("ms_sieve", ctypes.c_double), ("ms_giant", ctypes.c_double),
+                ("launches", ctypes.c_int), ("sm_count", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile libeis_gb300.so for sm_103a (nvcc) if it is out of date."""
+    return _build.build(force=force)
+
+
+# (name, restype, argtypes) of every exported symbol declared in include/eis.h
+_VP, _U64, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+_P = ctypes.POINTER
+SIGNATURES = [
+    ("eis_create", _I32, [_P(_VP), _I32, _U64]),
+    ("eis_destroy", _I32, [_VP]),
+    ("eis_strerror", ctypes.c_char_p, [_I32]),
+    ("eis_last_cuda_error_string", ctypes.c_char_p, []),
+    ("eis_set_option", _I32, [_VP, _I32, _I64]),
+    ("eis_get_option", _I32, [_VP, _I32, _P(_I64)]),
+    ("eis_get_stats", _I32, [_VP, _P(Stats)]),
+    ("eis_count_range", _I32, [_VP, _U64, _U64, _P(_U64)]),
+    ("eis_classify_range", _I32, [_VP, _U64, _U64, _VP, _VP, _I32, _P(_U64), _VP]),
+    ("eis_classify_range_u8", _I32, [_VP, _U64, _U64, _VP, _I32, _P(_U64), _VP]),
+    ("eis_classify_range_log", _I32, [_VP, _U64, _U64, _VP, _I32, _VP]),
+    ("eis_is_eisenstein", _I32, [_VP, _U64, _P(_I32)]),
+    ("eis_count_batch", _I32, [_VP, _VP, _VP, _SZ, _VP]),
+    ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
+    ("eis_plan_launch", _I32, [_VP, _VP]),
+    ("eis_plan_counts", _I32, [_VP, _VP]),
+    ("eis_plan_bitmaps", _I32, [_VP, _P(_VP), _P(_VP), _VP, _P(_U64)]),
+    ("eis_plan_stats", _I32, [_VP, _P(Stats)]),
+    ("eis_plan_destroy", _I32, [_VP]),
+]
+
+
+def lib():
+    """Load libeis_gb300.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libeis_gb300.so is not built; run "
+                                   "paper_2507_06579_gb300.build() (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != EIS_OK:
+        raise EisError(rc, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _u64_array(vals):
+    a = np.ascontiguousarray(np.asarray(vals, dtype=np.uint64))
+    return a
+
+
+def num_candidates(lo: int, hi: int):
+    """(n, d0): candidates d == 5 (mod 8) in [lo, hi) and the first one."""
+    d0 = lo + ((13 - lo % 8) % 8)
+    return (max(0, (hi - d0 + 7) // 8) if hi > d0 else 0), d0
+
+
+class Plan:
+    """A device-resident pipeline over fixed intervals (eis_plan_*)."""
+
+    def __init__(self, ctx: "Context", los, his, mode: int):
+        self.ctx = ctx
+        self.los = _u64_array(los)
+        self.his = _u64_array(his)
+        self.n = len(self.los)
+        h = ctypes.c_void_p()
+        _check(lib().eis_plan_create(ctx.handle, self.los.ctypes.data, self.his.ctypes.data,
+                                     self.n, mode, ctypes.byref(h)), "eis_plan_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().eis_plan_launch(self.handle, _stream_handle(stream)), "eis_plan_launch")
+
+    def counts(self):
+        out = np.zeros(max(self.n, 1), dtype=np.uint64)
+        _check(lib().eis_plan_counts(self.handle, out.ctypes.data), "eis_plan_counts")
+        return out[: self.n]
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().eis_plan_stats(self.handle, ctypes.byref(st)), "eis_plan_stats")
+        return st.as_dict()
+
+    def bitmaps(self):
+        """(flags_ptr, sqfree_ptr, word_offsets, total_words) -- device pointers."""
+        f, s = ctypes.c_void_p(), ctypes.c_void_p()
+        off = np.zeros(max(self.n, 1), dtype=np.uint64)
+        tot = ctypes.c_uint64()
+        _check(lib().eis_plan_bitmaps(self.handle, ctypes.byref(f), ctypes.byref(s),
+                                      off.ctypes.data, ctypes.byref(tot)), "eis_plan_bitmaps")
+        return f.value, s.value, off[: self.n], int(tot.value)
+
+    def destroy(self):
+        if self.handle:
+            lib().eis_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Context:
+    """One device context (eis_create / eis_destroy)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, mode: int | None = None):
+        h = ctypes.c_void_p()
+        _check(lib().eis_create(ctypes.byref(h), device, mem_budget_bytes), "eis_create")
+        self.handle = h
+        self.device = device
+        if mode is not None:
+            self.set_option(EIS_OPT_MODE, mode)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().eis_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- options / stats
+    def set_option(self, key: int, value: int):
+        _check(lib().eis_set_option(self.handle, key, int(value)), "eis_set_option")
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        _check(lib().eis_get_option(self.handle, key, ctypes.byref(v)), "eis_get_option")
+        return int(v.value)
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().eis_get_stats(self.handle, ctypes.byref(st)), "eis_get_stats")
+        return st.as_dict()
+
+    # -- entry points
+    def count_range(self, lo: int, hi: int) -> int:
+        out = ctypes.c_uint64()
+        _check(lib().eis_count_range(self.handle, lo, hi, ctypes.byref(out)), "eis_count_range")
+        return int(out.value)
+
+    def pi_E(self, x: int) -> int:
+        """pi_E(x) = #{d in E : d <= x}."""
+        return self.count_range(0, x + 1)
+
+    def classify_range(self, lo: int, hi: int, flags_out=None, sqfree_out=None, stream=None):
+        """Bit-packed flags / square-free words.  With no outputs given, returns
+        host numpy uint32 arrays (flags, sqfree, count).  Torch CUDA tensors as
+        outputs are written on the device."""
+        n, _ = num_candidates(lo, hi)
+        nw = (n + 31) // 32
+        cnt = ctypes.c_uint64()
+        if flags_out is None and sqfree_out is None:
+            f = np.zeros(max(nw, 1), dtype=np.uint32)
+            s = np.zeros(max(nw, 1), dtype=np.uint32)
+            _check(lib().eis_classify_range(self.handle, lo, hi, f.ctypes.data, s.ctypes.data, 0,
+                                            ctypes.byref(cnt), _stream_handle(stream)),
+                   "eis_classify_range")
+            return f[:nw], s[:nw], int(cnt.value)
+        on_dev = 1 if _is_device(flags_out if flags_out is not None else sqfree_out) else 0
+        _check(lib().eis_classify_range(self.handle, lo, hi, _ptr(flags_out), _ptr(sqfree_out),
+                                        on_dev, ctypes.byref(cnt), _stream_handle(stream)),
+               "eis_classify_range")
+        return flags_out, sqfree_out, int(cnt.value)
+
+    def classify_range_u8(self, lo: int, hi: int, codes_out=None, stream=None):
+        n, _ = num_candidates(lo, hi)
+        cnt = ctypes.c_uint64()
+        if codes_out is None:
+            codes = np.zeros(max(n, 1), dtype=np.uint8)
+            _check(lib().eis_classify_range_u8(self.handle, lo, hi, codes.ctypes.data, 0,
+                                               ctypes.byref(cnt), _stream_handle(stream)),
+                   "eis_classify_range_u8")
+            return codes[:n], int(cnt.value)
+        _check(lib().eis_classify_range_u8(self.handle, lo, hi, _ptr(codes_out),
+                                           1 if _is_device(codes_out) else 0, ctypes.byref(cnt),
+                                           _stream_handle(stream)), "eis_classify_range_u8")
+        return codes_out, int(cnt.value)
+
+    def classify_range_log(self, lo: int, hi: int, stream=None):
+        n, _ = num_candidates(lo, hi)
+        out = np.zeros(max(n, 1), dtype=np.uint8)
+        _check(lib().eis_classify_range_log(self.handle, lo, hi, out.ctypes.data, 0,
+                                            _stream_handle(stream)), "eis_classify_range_log")
+        return out[:n]
+
+    def is_eisenstein(self, d: int) -> bool:
+        r = ctypes.c_int()
+        _check(lib().eis_is_eisenstein(self.handle, d, ctypes.byref(r)), "eis_is_eisenstein")
+        return bool(r.value)
+
+    def count_batch(self, los, his):
+        lo = _u64_array(los)
+        hi = _u64_array(his)
+        assert lo.shape == hi.shape
+        out = np.zeros(max(len(lo), 1), dtype=np.uint64)
+        _check(lib().eis_count_batch(self.handle, lo.ctypes.data, hi.ctypes.data, len(lo),
+                                     out.ctypes.data), "eis_count_batch")
+        return out[: len(lo)]
+
+    def plan_create(self, los, his, mode: int = EIS_MODE_PERSISTENT) -> Plan:
+        return Plan(self, los, his, mode)
+
+
+def _is_device(t) -> bool:
+    return hasattr(t, "is_cuda") and bool(t.is_cuda)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t)

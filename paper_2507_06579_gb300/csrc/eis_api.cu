@@ -1,0 +1,760 @@
+// eis_api.cu -- host runtime behind the C-ABI of include/eis.h: contexts,
+// plans (device-resident pipelines captured into CUDA graphs) and the
+// convenience calls.  All device memory of a pipeline is allocated when the
+// plan is created; eis_plan_launch only enqueues kernels (or one graph).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "eis.h"
+#include "eis_kernels.h"
+
+using namespace eis;
+
+#define EIS_CK(call)                                            \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) {                                \
+            eis_last_cuda_error = e_;                           \
+            return EIS_EDEVICE;                                 \
+        }                                                       \
+    } while (0)
+
+static thread_local cudaError_t eis_last_cuda_error = cudaSuccess;
+
+extern "C" const char *eis_last_cuda_error_string(void) {
+    return cudaGetErrorString(eis_last_cuda_error);
+}
+
+struct eis_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    uint64_t in_use = 0;
+    uint32_t *d_primes = nullptr;
+    uint32_t nprimes = 0;
+    int *d_single = nullptr;  // [0] result, [1] steps, [2] status
+    int mode = EIS_MODE_PERSISTENT;
+    int ctas_per_sm = 0;
+    int threads = 256;
+    int64_t step_limit = (int64_t)1 << 26;  // >> any half period below 2^44
+    int use_graph = 1;
+    int64_t giant_threshold = 0;
+    int64_t giant_stride = 0;
+    int occ_persistent = 1;
+    eis_stats last{};
+};
+
+struct PlainBlock {
+    uint64_t d_first, cand_first;
+    uint32_t ncand;
+};
+
+struct eis_plan {
+    eis_ctx *ctx = nullptr;
+    int mode = EIS_MODE_PERSISTENT;
+    size_t n = 0;
+    std::vector<Seg> segs;              // layout order (sorted by d0)
+    std::vector<uint32_t> user_of;      // layout index -> user index
+    std::vector<uint64_t> word_off;     // user index -> first word
+    std::vector<Tile> tiles;
+    std::vector<PlainBlock> blocks;
+    uint64_t total_cand = 0, nwords = 0;
+    Seg *d_segs = nullptr;
+    Tile *d_tiles = nullptr;
+    uint32_t *d_sqfree = nullptr, *d_flags = nullptr;
+    uint32_t *d_tile_pop = nullptr, *d_tile_off = nullptr, *d_surv = nullptr;
+    uint32_t *d_ctr = nullptr;  // [0] survivors, [1] queue head
+    int *d_status = nullptr;
+    unsigned long long *d_counts = nullptr;  // [2 s] #E, [2 s + 1] #D
+    unsigned long long *d_steps = nullptr;   // [0] baby, [1] giant, [2] deferred
+    uint8_t *d_glog = nullptr;
+    uint64_t bytes = 0;
+    uint32_t walk_grid = 0;
+    int launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static int plan_alloc(eis_plan *p, void **ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (p->ctx->in_use + bytes > p->ctx->budget) return EIS_ENOMEM;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return EIS_ENOMEM;
+    }
+    p->ctx->in_use += bytes;
+    p->bytes += bytes;
+    return EIS_OK;
+}
+
+static uint64_t num_candidates(uint64_t lo, uint64_t hi, uint64_t *d0) {
+    const uint64_t first = lo + ((13 - lo % 8) % 8);
+    *d0 = first;
+    return hi > first ? (hi - first + 7) / 8 : 0;
+}
+
+static std::vector<uint32_t> odd_primes_below(uint32_t n) {
+    std::vector<uint8_t> comp(n, 0);
+    std::vector<uint32_t> out;
+    for (uint32_t i = 2; i < n; ++i) {
+        if (comp[i]) continue;
+        if (i > 2) out.push_back(i);
+        for (uint64_t j = (uint64_t)i * i; j < n; j += i) comp[j] = 1;
+    }
+    return out;
+}
+
+// Bytes a plan needs per candidate: survivor queue (4) + two bitmaps (1/4),
+// plus the optional per-candidate log byte.
+static uint64_t max_chunk_cands(const eis_ctx *c, int with_log) {
+    const uint64_t free_b = c->budget > c->in_use ? c->budget - c->in_use : 0;
+    uint64_t m = free_b / (5 + (uint64_t)with_log + 1);
+    m = std::min<uint64_t>(m, (uint64_t)1 << 31);
+    m -= m % kTileCands;
+    return m;
+}
+
+static void record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
+    if (capturing)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
+
+static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
+    eis_ctx *c = p->ctx;
+    const uint32_t nseg = (uint32_t)p->segs.size();
+    const uint32_t ntiles = (uint32_t)p->tiles.size();
+    const uint32_t limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
+    int launches = 0;
+    record(p->ev[0], s, capturing);
+    EIS_CK(cudaMemsetAsync(p->d_flags, 0, p->nwords * 4, s));
+    EIS_CK(cudaMemsetAsync(p->d_ctr, 0, 4 * sizeof(uint32_t), s));
+    EIS_CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    EIS_CK(cudaMemsetAsync(p->d_counts, 0, 2 * nseg * sizeof(unsigned long long) + 8, s));
+    EIS_CK(cudaMemsetAsync(p->d_steps, 0, 4 * sizeof(unsigned long long), s));
+    if (p->d_glog) EIS_CK(cudaMemsetAsync(p->d_glog, 0, p->total_cand, s));
+    if (ntiles > 0) {
+        k_sieve<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_segs, c->d_primes, c->nprimes, p->d_sqfree,
+                                       p->d_tile_pop);
+        ++launches;
+        if (p->mode == EIS_MODE_PERSISTENT) {
+            k_scan_tiles<<<1, 1024, 0, s>>>(p->d_tile_pop, p->d_tile_off, ntiles, p->d_ctr);
+            k_compact<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_sqfree, p->d_tile_off, p->d_surv);
+            launches += 2;
+            record(p->ev[1], s, capturing);
+            k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(p->d_segs, nseg, p->d_surv, p->d_ctr,
+                                                           p->d_ctr + 1, p->d_flags, p->d_glog,
+                                                           p->d_steps, p->d_status, limit);
+            ++launches;
+            record(p->ev[2], s, capturing);
+        } else {
+            record(p->ev[1], s, capturing);
+            for (const PlainBlock &b : p->blocks) {
+                const uint32_t grid = (b.ncand + 255) / 256;
+                k_walk_plain<<<grid, 256, 0, s>>>(b.d_first, b.cand_first, b.ncand, p->d_sqfree,
+                                                  p->d_flags, p->d_glog, p->d_steps, p->d_status,
+                                                  limit);
+                ++launches;
+            }
+            record(p->ev[2], s, capturing);
+        }
+        k_count<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_flags, p->d_sqfree, p->d_counts);
+        ++launches;
+    } else {
+        record(p->ev[1], s, capturing);
+        record(p->ev[2], s, capturing);
+    }
+    record(p->ev[3], s, capturing);
+    EIS_CK(cudaGetLastError());
+    p->launches = launches;
+    return EIS_OK;
+}
+
+static void plan_free(eis_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto &e : p->ev)
+        if (e) cudaEventDestroy(e);
+    void *bufs[] = {p->d_segs, p->d_tiles, p->d_sqfree, p->d_flags, p->d_tile_pop, p->d_tile_off,
+                    p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (p->ctx) p->ctx->in_use -= std::min(p->ctx->in_use, p->bytes);
+    delete p;
+}
+
+static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
+                      int with_log, eis_plan **out) {
+    if (!c || !out || (n && (!lo || !hi))) return EIS_EINVAL;
+    if (mode != EIS_MODE_PLAIN && mode != EIS_MODE_PERSISTENT) return EIS_EINVAL;
+    for (size_t i = 0; i < n; ++i) {
+        if (lo[i] > hi[i]) return EIS_EINVAL;
+        if (hi[i] > EIS_D_LIMIT) return EIS_ERANGE;
+    }
+    EIS_CK(cudaSetDevice(c->device));
+    eis_plan *p = new eis_plan();
+    p->ctx = c;
+    p->mode = mode;
+    p->n = n;
+    std::vector<uint64_t> d0(n), nc(n);
+    for (size_t i = 0; i < n; ++i) nc[i] = num_candidates(lo[i], hi[i], &d0[i]);
+    std::vector<uint32_t> order(n);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return d0[a] < d0[b]; });
+    p->word_off.assign(n, 0);
+    uint64_t cur = 0;
+    for (uint32_t u : order) {
+        Seg s{d0[u], nc[u], cur};
+        p->segs.push_back(s);
+        p->user_of.push_back(u);
+        p->word_off[u] = cur / 32;
+        cur += (nc[u] + 31) / 32 * 32;
+    }
+    p->total_cand = cur;
+    p->nwords = cur / 32;
+    // Survivor indices are 32-bit and the queue head may overshoot by one
+    // claim per warp.
+    if (cur > 0xffffffffull - (1ull << 24)) {
+        plan_free(p);
+        return EIS_ENOMEM;
+    }
+    for (uint32_t si = 0; si < p->segs.size(); ++si) {
+        const Seg &s = p->segs[si];
+        for (uint64_t off = 0; off < s.ncand; off += kTileCands) {
+            Tile t{s.cand0 + off, si, (uint32_t)std::min<uint64_t>(kTileCands, s.ncand - off)};
+            p->tiles.push_back(t);
+        }
+        for (uint64_t off = 0; off < s.ncand; off += kPlainBlockCands) {
+            PlainBlock b{s.d0 + 8 * off, s.cand0 + off,
+                         (uint32_t)std::min<uint64_t>(kPlainBlockCands, s.ncand - off)};
+            p->blocks.push_back(b);
+        }
+    }
+    int rc = EIS_OK;
+    const size_t nseg = p->segs.size(), ntiles = p->tiles.size();
+#define EIS_ALLOC(ptr, bytes)                                             \
+    do {                                                                  \
+        rc = plan_alloc(p, (void **)&(ptr), (bytes));                     \
+        if (rc != EIS_OK) {                                               \
+            plan_free(p);                                                 \
+            return rc;                                                    \
+        }                                                                 \
+    } while (0)
+    EIS_ALLOC(p->d_segs, nseg * sizeof(Seg));
+    EIS_ALLOC(p->d_tiles, ntiles * sizeof(Tile));
+    EIS_ALLOC(p->d_sqfree, p->nwords * 4);
+    EIS_ALLOC(p->d_flags, p->nwords * 4);
+    EIS_ALLOC(p->d_tile_pop, ntiles * 4);
+    EIS_ALLOC(p->d_tile_off, ntiles * 4);
+    if (mode == EIS_MODE_PERSISTENT) EIS_ALLOC(p->d_surv, p->total_cand * 4);
+    EIS_ALLOC(p->d_ctr, 4 * sizeof(uint32_t));
+    EIS_ALLOC(p->d_status, sizeof(int));
+    EIS_ALLOC(p->d_counts, 2 * nseg * sizeof(unsigned long long) + 8);
+    EIS_ALLOC(p->d_steps, 4 * sizeof(unsigned long long));
+    if (with_log) EIS_ALLOC(p->d_glog, p->total_cand);
+#undef EIS_ALLOC
+    for (auto &e : p->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            plan_free(p);
+            return EIS_EDEVICE;
+        }
+    }
+    if (nseg && cudaMemcpy(p->d_segs, p->segs.data(), nseg * sizeof(Seg), cudaMemcpyHostToDevice) != cudaSuccess) {
+        plan_free(p);
+        return EIS_EDEVICE;
+    }
+    if (ntiles && cudaMemcpy(p->d_tiles, p->tiles.data(), ntiles * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess) {
+        plan_free(p);
+        return EIS_EDEVICE;
+    }
+    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : c->occ_persistent;
+    p->walk_grid = (uint32_t)(c->sm_count * std::max(1, per_sm));
+    if (c->use_graph) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            plan_free(p);
+            return EIS_EDEVICE;
+        }
+        rc = plan_enqueue(p, c->stream, true);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc != EIS_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            plan_free(p);
+            return rc != EIS_OK ? rc : EIS_EDEVICE;
+        }
+        p->graph = g;
+        if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+            plan_free(p);
+            return EIS_EDEVICE;
+        }
+    }
+    *out = p;
+    return EIS_OK;
+}
+
+static int plan_launch(eis_plan *p, cudaStream_t s) {
+    EIS_CK(cudaSetDevice(p->ctx->device));
+    if (!s) s = p->ctx->stream;
+    if (p->exec) {
+        EIS_CK(cudaGraphLaunch(p->exec, s));
+    } else {
+        int rc = plan_enqueue(p, s, false);
+        if (rc != EIS_OK) return rc;
+    }
+    p->last_stream = s;
+    p->launched = true;
+    return EIS_OK;
+}
+
+static int plan_wait(eis_plan *p) {
+    if (!p->launched) return EIS_EINVAL;
+    EIS_CK(cudaStreamSynchronize(p->last_stream));
+    int status = 0;
+    EIS_CK(cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & kErrSteps) return EIS_ESTEPS;
+    return EIS_OK;
+}
+
+static int plan_fill_stats(eis_plan *p, eis_stats *st) {
+    int rc = plan_wait(p);
+    if (rc != EIS_OK) return rc;
+    std::memset(st, 0, sizeof(*st));
+    unsigned long long steps[4] = {0, 0, 0, 0};
+    EIS_CK(cudaMemcpy(steps, p->d_steps, sizeof(steps), cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> cnt(2 * p->segs.size() + 1);
+    EIS_CK(cudaMemcpy(cnt.data(), p->d_counts, cnt.size() * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < p->segs.size(); ++i) {
+        st->candidates += p->segs[i].ncand;
+        st->in_E += cnt[2 * i];
+        st->in_D += cnt[2 * i + 1];
+    }
+    st->baby_steps = steps[0];
+    st->giant_steps = steps[1];
+    st->deferred = steps[2];
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[3]) == cudaSuccess) st->ms_total = ms;
+    if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) st->ms_sieve = ms;
+    if (cudaEventElapsedTime(&ms, p->ev[1], p->ev[2]) == cudaSuccess) st->ms_walk = ms;
+    cudaGetLastError();
+    st->launches = p->launches;
+    st->sm_count = p->ctx->sm_count;
+    return EIS_OK;
+}
+
+static int plan_counts_user(eis_plan *p, uint64_t *counts_out) {
+    int rc = plan_wait(p);
+    if (rc != EIS_OK) return rc;
+    std::vector<unsigned long long> cnt(2 * p->segs.size() + 1);
+    EIS_CK(cudaMemcpy(cnt.data(), p->d_counts, cnt.size() * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < p->segs.size(); ++i) counts_out[p->user_of[i]] = cnt[2 * i];
+    return EIS_OK;
+}
+
+// Run [lo, hi) in chunks of at most M candidates (M a multiple of the tile
+// size, so chunk j starts at candidate j*M and at output word j*M/32).  The
+// callback gets each finished chunk's plan and candidate offset.
+template <class F>
+static int run_chunks(eis_ctx *c, uint64_t lo, uint64_t hi, int with_log, cudaStream_t s,
+                      eis_stats *acc, F &&on_chunk) {
+    if (!c || lo > hi) return EIS_EINVAL;
+    if (hi > EIS_D_LIMIT) return EIS_ERANGE;
+    uint64_t d0;
+    const uint64_t ntot = num_candidates(lo, hi, &d0);
+    const uint64_t M = max_chunk_cands(c, with_log);
+    if (M == 0) return EIS_ENOMEM;
+    std::memset(acc, 0, sizeof(*acc));
+    for (uint64_t off = 0; off < ntot || (off == 0 && ntot == 0); off += M) {
+        const uint64_t a = lo + 8 * off;
+        const uint64_t b = std::min(hi, lo + 8 * (off + M));
+        eis_plan *p = nullptr;
+        int rc = plan_build(c, &a, &b, 1, c->mode, with_log, &p);
+        if (rc != EIS_OK) return rc;
+        rc = plan_launch(p, s);
+        eis_stats st{};
+        if (rc == EIS_OK) rc = plan_fill_stats(p, &st);
+        if (rc == EIS_OK) rc = on_chunk(p, off);
+        plan_free(p);
+        if (rc != EIS_OK) return rc;
+        acc->candidates += st.candidates;
+        acc->in_D += st.in_D;
+        acc->in_E += st.in_E;
+        acc->baby_steps += st.baby_steps;
+        acc->giant_steps += st.giant_steps;
+        acc->deferred += st.deferred;
+        acc->ms_total += st.ms_total;
+        acc->ms_walk += st.ms_walk;
+        acc->ms_sieve += st.ms_sieve;
+        acc->ms_giant += st.ms_giant;
+        acc->launches += st.launches;
+        acc->sm_count = st.sm_count;
+        if (ntot == 0) break;
+    }
+    return EIS_OK;
+}
+
+// ------------------------------------------------------------------ C-ABI
+
+extern "C" {
+
+const char *eis_strerror(int code) {
+    switch (code) {
+        case EIS_OK: return "ok";
+        case EIS_EINVAL: return "invalid argument";
+        case EIS_ENOTD: return "d is not a square-free d == 5 (mod 8)";
+        case EIS_ERANGE: return "value above the supported limit 2^44";
+        case EIS_ENOMEM: return "out of memory or over the context's budget";
+        case EIS_ETIMEOUT: return "wait timed out";
+        case EIS_EDEVICE: return "CUDA error";
+        case EIS_ESTEPS: return "a walk ran past its step limit";
+        case EIS_EBUSY: return "request not admitted";
+        case EIS_ENOTFOUND: return "unknown request";
+        default: return "unknown error";
+    }
+}
+
+int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
+    if (!out) return EIS_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    EIS_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return EIS_EINVAL;
+    EIS_CK(cudaSetDevice(device));
+    eis_ctx *c = new eis_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return EIS_EDEVICE;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete c;
+        return EIS_EDEVICE;
+    }
+    c->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)free_b / 4 * 3;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return EIS_EDEVICE;
+    }
+    std::vector<uint32_t> pr = odd_primes_below(1u << 22);
+    c->nprimes = (uint32_t)pr.size();
+    if (cudaMalloc(&c->d_primes, pr.size() * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_single, 4 * sizeof(int)) != cudaSuccess) {
+        eis_destroy(c);
+        return EIS_ENOMEM;
+    }
+    c->in_use = pr.size() * 4 + 4 * sizeof(int);
+    if (cudaMemcpy(c->d_primes, pr.data(), pr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        eis_destroy(c);
+        return EIS_EDEVICE;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_persistent, 256, 0) != cudaSuccess)
+        occ = 1;
+    c->occ_persistent = std::max(1, occ);
+    *out = c;
+    return EIS_OK;
+}
+
+int eis_destroy(eis_ctx *c) {
+    if (!c) return EIS_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->d_primes) cudaFree(c->d_primes);
+    if (c->d_single) cudaFree(c->d_single);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return EIS_OK;
+}
+
+int eis_set_option(eis_ctx *c, int key, int64_t v) {
+    if (!c) return EIS_EINVAL;
+    switch (key) {
+        case EIS_OPT_MODE:
+            if (v != EIS_MODE_PLAIN && v != EIS_MODE_PERSISTENT) return EIS_EINVAL;
+            c->mode = (int)v;
+            return EIS_OK;
+        case EIS_OPT_CTAS_PER_SM:
+            if (v < 0 || v > 64) return EIS_EINVAL;
+            c->ctas_per_sm = (int)v;
+            return EIS_OK;
+        case EIS_OPT_THREADS:
+            if (v != 256) return EIS_EINVAL;
+            c->threads = (int)v;
+            return EIS_OK;
+        case EIS_OPT_STEP_LIMIT:
+            if (v < 1 || v > 0xffffffffll) return EIS_EINVAL;
+            c->step_limit = v;
+            return EIS_OK;
+        case EIS_OPT_USE_GRAPH:
+            c->use_graph = v ? 1 : 0;
+            return EIS_OK;
+        case EIS_OPT_GIANT_THRESHOLD:
+            if (v < 0) return EIS_EINVAL;
+            c->giant_threshold = v;
+            return EIS_OK;
+        case EIS_OPT_GIANT_STRIDE:
+            if (v < 0) return EIS_EINVAL;
+            c->giant_stride = v;
+            return EIS_OK;
+        default:
+            return EIS_EINVAL;
+    }
+}
+
+int eis_get_option(eis_ctx *c, int key, int64_t *v) {
+    if (!c || !v) return EIS_EINVAL;
+    switch (key) {
+        case EIS_OPT_MODE: *v = c->mode; return EIS_OK;
+        case EIS_OPT_CTAS_PER_SM: *v = c->ctas_per_sm ? c->ctas_per_sm : c->occ_persistent; return EIS_OK;
+        case EIS_OPT_THREADS: *v = c->threads; return EIS_OK;
+        case EIS_OPT_STEP_LIMIT: *v = c->step_limit; return EIS_OK;
+        case EIS_OPT_USE_GRAPH: *v = c->use_graph; return EIS_OK;
+        case EIS_OPT_GIANT_THRESHOLD: *v = c->giant_threshold; return EIS_OK;
+        case EIS_OPT_GIANT_STRIDE: *v = c->giant_stride; return EIS_OK;
+        default: return EIS_EINVAL;
+    }
+}
+
+int eis_get_stats(eis_ctx *c, eis_stats *out) {
+    if (!c || !out) return EIS_EINVAL;
+    *out = c->last;
+    return EIS_OK;
+}
+
+int eis_plan_create(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
+                    eis_plan **out) {
+    return plan_build(c, lo, hi, n, mode, 0, out);
+}
+
+int eis_plan_launch(eis_plan *p, void *stream) {
+    if (!p) return EIS_EINVAL;
+    return plan_launch(p, (cudaStream_t)stream);
+}
+
+int eis_plan_counts(eis_plan *p, uint64_t *counts_out) {
+    if (!p || (!counts_out && p->n)) return EIS_EINVAL;
+    return plan_counts_user(p, counts_out);
+}
+
+int eis_plan_bitmaps(eis_plan *p, const uint32_t **flags, const uint32_t **sqfree,
+                     uint64_t *word_offset, uint64_t *total_words) {
+    if (!p) return EIS_EINVAL;
+    if (flags) *flags = p->d_flags;
+    if (sqfree) *sqfree = p->d_sqfree;
+    if (word_offset)
+        for (size_t i = 0; i < p->n; ++i) word_offset[i] = p->word_off[i];
+    if (total_words) *total_words = p->nwords;
+    return EIS_OK;
+}
+
+int eis_plan_stats(eis_plan *p, eis_stats *out) {
+    if (!p || !out) return EIS_EINVAL;
+    return plan_fill_stats(p, out);
+}
+
+int eis_plan_destroy(eis_plan *p) {
+    if (!p) return EIS_OK;
+    cudaSetDevice(p->ctx->device);
+    if (p->launched) cudaStreamSynchronize(p->last_stream);
+    plan_free(p);
+    return EIS_OK;
+}
+
+int eis_count_range(eis_ctx *c, uint64_t lo, uint64_t hi, uint64_t *count_out) {
+    if (!c || !count_out) return EIS_EINVAL;
+    eis_stats acc{};
+    int rc = run_chunks(c, lo, hi, 0, c->stream, &acc, [](eis_plan *, uint64_t) { return EIS_OK; });
+    if (rc != EIS_OK) return rc;
+    c->last = acc;
+    *count_out = acc.in_E;
+    return EIS_OK;
+}
+
+int eis_classify_range(eis_ctx *c, uint64_t lo, uint64_t hi, uint32_t *flags_out,
+                       uint32_t *sqfree_out, int out_on_device, uint64_t *count_out,
+                       void *stream) {
+    if (!c) return EIS_EINVAL;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    eis_stats acc{};
+    int rc = run_chunks(c, lo, hi, 0, s, &acc, [&](eis_plan *p, uint64_t off) -> int {
+        const uint64_t w0 = off / 32;
+        if (flags_out && p->nwords)
+            EIS_CK(cudaMemcpyAsync(flags_out + w0, p->d_flags, p->nwords * 4, kind, s));
+        if (sqfree_out && p->nwords)
+            EIS_CK(cudaMemcpyAsync(sqfree_out + w0, p->d_sqfree, p->nwords * 4, kind, s));
+        EIS_CK(cudaStreamSynchronize(s));
+        return EIS_OK;
+    });
+    if (rc != EIS_OK) return rc;
+    c->last = acc;
+    if (count_out) *count_out = acc.in_E;
+    return EIS_OK;
+}
+
+int eis_classify_range_u8(eis_ctx *c, uint64_t lo, uint64_t hi, uint8_t *codes_out,
+                          int out_on_device, uint64_t *count_out, void *stream) {
+    if (!c || !codes_out) return EIS_EINVAL;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    uint64_t d0;
+    const uint64_t ntot = num_candidates(lo, hi, &d0);
+    eis_stats acc{};
+    int rc = run_chunks(c, lo, hi, 1, s, &acc, [&](eis_plan *p, uint64_t off) -> int {
+        const uint64_t n = std::min<uint64_t>(p->total_cand, ntot - off);
+        if (n == 0) return EIS_OK;
+        uint8_t *tmp = out_on_device ? codes_out + off : nullptr;
+        if (!tmp) {
+            if (cudaMalloc(&tmp, n) != cudaSuccess) {
+                cudaGetLastError();
+                return EIS_ENOMEM;
+            }
+        }
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 65535ull * 8);
+        k_expand_codes<<<grid, 256, 0, s>>>(p->d_flags, p->d_sqfree, n, tmp);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !out_on_device)
+            e = cudaMemcpyAsync(codes_out + off, tmp, n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (!out_on_device) cudaFree(tmp);
+        (void)kind;
+        return e == cudaSuccess ? EIS_OK : EIS_EDEVICE;
+    });
+    if (rc != EIS_OK) return rc;
+    c->last = acc;
+    if (count_out) *count_out = acc.in_E;
+    return EIS_OK;
+}
+
+int eis_classify_range_log(eis_ctx *c, uint64_t lo, uint64_t hi, uint8_t *log_out,
+                           int out_on_device, void *stream) {
+    if (!c || !log_out) return EIS_EINVAL;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    uint64_t d0;
+    const uint64_t ntot = num_candidates(lo, hi, &d0);
+    eis_stats acc{};
+    int rc = run_chunks(c, lo, hi, 1, s, &acc, [&](eis_plan *p, uint64_t off) -> int {
+        const uint64_t n = std::min<uint64_t>(p->total_cand, ntot - off);
+        if (n) EIS_CK(cudaMemcpyAsync(log_out + off, p->d_glog, n, kind, s));
+        EIS_CK(cudaStreamSynchronize(s));
+        return EIS_OK;
+    });
+    if (rc != EIS_OK) return rc;
+    c->last = acc;
+    return EIS_OK;
+}
+
+int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
+    if (!c || !result_out) return EIS_EINVAL;
+    if (d >= EIS_D_LIMIT) return EIS_ERANGE;
+    if (d % 8 != 5) return EIS_ENOTD;
+    EIS_CK(cudaSetDevice(c->device));
+    const uint32_t limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
+    EIS_CK(cudaMemsetAsync(c->d_single, 0, 4 * sizeof(int), c->stream));
+    k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->nprimes, c->d_single,
+                                           c->d_single + 2, limit);
+    EIS_CK(cudaGetLastError());
+    int h[4] = {0, 0, 0, 0};
+    EIS_CK(cudaMemcpyAsync(h, c->d_single, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    EIS_CK(cudaStreamSynchronize(c->stream));
+    if (h[2] & kErrSteps) return EIS_ESTEPS;
+    std::memset(&c->last, 0, sizeof(c->last));
+    c->last.candidates = 1;
+    c->last.baby_steps = (uint64_t)h[1];
+    if (h[0] == 0) return EIS_ENOTD;
+    c->last.in_D = 1;
+    c->last.in_E = (h[0] == 1);
+    *result_out = (h[0] == 1) ? 1 : 0;
+    return EIS_OK;
+}
+
+int eis_count_batch(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n,
+                    uint64_t *counts_out) {
+    if (!c || (n && (!lo || !hi || !counts_out))) return EIS_EINVAL;
+    for (size_t i = 0; i < n; ++i) {
+        if (lo[i] > hi[i]) return EIS_EINVAL;
+        if (hi[i] > EIS_D_LIMIT) return EIS_ERANGE;
+    }
+    const uint64_t M = max_chunk_cands(c, 0);
+    if (M == 0) return EIS_ENOMEM;
+    eis_stats acc{};
+    // Group intervals into plans of at most M candidates; an interval larger
+    // than M is counted on its own in chunks.
+    size_t i = 0;
+    while (i < n) {
+        std::vector<uint64_t> glo, ghi;
+        std::vector<size_t> gidx;
+        uint64_t tot = 0;
+        while (i < n) {
+            uint64_t d0;
+            const uint64_t nc = (num_candidates(lo[i], hi[i], &d0) + 31) / 32 * 32;
+            if (nc > M) {
+                if (!gidx.empty()) break;
+                uint64_t v = 0;
+                int rc = eis_count_range(c, lo[i], hi[i], &v);
+                if (rc != EIS_OK) return rc;
+                counts_out[i] = v;
+                const eis_stats st = c->last;
+                acc.candidates += st.candidates;
+                acc.in_D += st.in_D;
+                acc.in_E += st.in_E;
+                acc.baby_steps += st.baby_steps;
+                acc.ms_total += st.ms_total;
+                acc.ms_walk += st.ms_walk;
+                acc.ms_sieve += st.ms_sieve;
+                acc.launches += st.launches;
+                ++i;
+                continue;
+            }
+            if (tot + nc > M) break;
+            tot += nc;
+            glo.push_back(lo[i]);
+            ghi.push_back(hi[i]);
+            gidx.push_back(i);
+            ++i;
+        }
+        if (gidx.empty()) continue;
+        eis_plan *p = nullptr;
+        int rc = plan_build(c, glo.data(), ghi.data(), glo.size(), c->mode, 0, &p);
+        if (rc != EIS_OK) return rc;
+        rc = plan_launch(p, c->stream);
+        std::vector<uint64_t> cnt(gidx.size());
+        eis_stats st{};
+        if (rc == EIS_OK) rc = plan_counts_user(p, cnt.data());
+        if (rc == EIS_OK) rc = plan_fill_stats(p, &st);
+        plan_free(p);
+        if (rc != EIS_OK) return rc;
+        for (size_t k = 0; k < gidx.size(); ++k) counts_out[gidx[k]] = cnt[k];
+        acc.candidates += st.candidates;
+        acc.in_D += st.in_D;
+        acc.in_E += st.in_E;
+        acc.baby_steps += st.baby_steps;
+        acc.ms_total += st.ms_total;
+        acc.ms_walk += st.ms_walk;
+        acc.ms_sieve += st.ms_sieve;
+        acc.launches += st.launches;
+        acc.sm_count = st.sm_count;
+    }
+    c->last = acc;
+    return EIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// eis_common.cuh -- device-side building blocks shared by the kernels.
+//
+// The baby step (Appendix A of Breuer & Punch): on the reduced ideal
+// [Q_j/2, (P_j + sqrt d)/2] of O_K, O_K = Z[(1+sqrt d)/2],
+//     q_j = floor((P_j + sqrt d)/Q_j),  P_{j+1} = q_j Q_j - P_j,
+//     Q_{j+1} = (d - P_{j+1}^2)/Q_j,
+//     theta_{j+2} = (P_{j+1} + sqrt d)/Q_j * theta_{j+1}.
+// The generator is kept in (O_K/2O_K)* = F_4* = Z/3 (Appendix A): the factor
+// (P_{j+1}+sqrt d)/Q_j = [(P_{j+1}-1)/2 + omega] * [Q_j/2]^(-1) with Q_j/2 odd
+// is omega (log 1) when P_{j+1} == 1 (mod 4) and omega + 1 = omega^2 (log 2)
+// when P_{j+1} == 3 (mod 4).  eps_d == 1 (mod 2O_K) iff the logs over one
+// period sum to 0 mod 3.
+//
+// Arithmetic: for d < 2^44 every quantity of a reduced state (P, Q, P + s with
+// s = floor(sqrt d), q Q, Q_{j+1} - Q_{j-1}) is an integer below 2^23, so the
+// walk runs in fp32 registers with every operation exact:
+//   * q from a hardware reciprocal estimate: 2^23 + floor(num * rcp(Q) - 1/2)
+//     by one FMA rounded toward -inf.  rcp.approx has at most 1 ulp error, so
+//     |num*rcp(Q) - num/Q| < num/Q * 2^-23 < 1/2 and the estimate is q or q-1;
+//     one compare of the remainder against Q corrects it.
+//   * Q_{j+1} by the recurrence Q_{j+1} = Q_{j-1} + q_j (P_j - P_{j+1}),
+//     which follows from Q_j Q_{j+1} = d - P_{j+1}^2 and Q_{j-1} Q_j = d - P_j^2
+//     (no division, no 64-bit product).
+//   * P is carried as P + 2^23, so the float's low mantissa bits are P itself
+//     and P mod 4 is one AND on the bit pattern.
+//
+// Half period: the P's and Q's of one period are palindromic,
+// Q_j = Q_{l-j} and P_j = P_{l+1-j}; the walk stops at the centre, which is
+// the first j with Q_{j+1} = Q_j (l = 2j+1) or P_{j+1} = P_j (l = 2j), the
+// test of Algorithm 1.  With S_j = sum_{i<=j} log(P_i):
+//   l = 2j+1: log eps = 2 S_j + log(P_{j+1});   l = 2j: log eps = 2 S_j.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eis {
+
+constexpr int kTileCands = 1 << 16;          // candidates per sieve tile
+constexpr int kTileWords = kTileCands / 32;  // bitmap words per tile
+constexpr int kPlainBlockCands = 1 << 21;    // 2^24-wide block of d = 2^21 candidates
+constexpr float kMagic = 8388608.0f;         // 2^23
+constexpr unsigned kFull = 0xffffffffu;
+
+// One interval of a plan, in the plan's candidate layout.
+struct Seg {
+    uint64_t d0;     // first candidate d (== 5 mod 8)
+    uint64_t ncand;  // number of candidates
+    uint64_t cand0;  // global index of candidate 0 (multiple of 32)
+};
+
+// A sieve / count tile: up to kTileCands consecutive candidates of one Seg.
+struct Tile {
+    uint64_t cand0;  // global candidate index of the first candidate (multiple of 32)
+    uint32_t seg;    // index into the Seg table
+    uint32_t ncand;  // candidates in this tile
+};
+
+// Error codes written by kernels into the plan's status word.
+constexpr int kErrSteps = 1;
+
+// floor(sqrt(d)) for d < 2^53: correctly rounded double sqrt, then exact
+// integer fix-ups (at most one step each way).
+__device__ __forceinline__ uint64_t isqrt_u64(uint64_t d) {
+    uint64_t s = (uint64_t)sqrt((double)d);
+    while (s * s > d) --s;
+    while ((s + 1) * (s + 1) <= d) ++s;
+    return s;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct WalkState {
+    float Pm;    // P_j + 2^23
+    float Q;     // Q_j
+    float Qp;    // Q_{j-1}
+    float soff;  // s - 2^23
+    float sm;    // s + 2^23
+    int acc2;    // 2 S_j (sum of 2*log over the states walked), not reduced
+};
+
+// A benign valid state (d = 5 at j = 1): stepping it is a fixed point.
+__device__ __forceinline__ void walk_park(WalkState &w) {
+    w.Pm = kMagic + 1.0f;
+    w.Q = 2.0f;
+    w.Qp = 2.0f;
+    w.soff = 2.0f - kMagic;
+    w.sm = 2.0f + kMagic;
+    w.acc2 = 0;
+}
+
+// First step from (P_0, Q_0) = (1, 2) in 64-bit integers: q_0 = floor((1+s)/2),
+// P_1 = 2 q_0 - 1, Q_1 = (d - P_1^2)/2.  Returns true when the period is 1
+// (Q_1 = Q_0 = 2), with *g = log eps_d; otherwise leaves the state at j = 1.
+__device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
+    const uint64_t s = isqrt_u64(d);
+    const uint64_t a0 = (1 + s) >> 1;
+    const uint64_t P1 = 2 * a0 - 1;
+    const uint64_t Q1 = (d - P1 * P1) >> 1;
+    const int c1 = 1 + (int)((P1 >> 1) & 1);  // log of (P_1 + sqrt d)/2 mod 2
+    if (Q1 == 2) {
+        g = c1;
+        return true;
+    }
+    w.Pm = __fadd_rn(__uint2float_rn((uint32_t)P1), kMagic);
+    w.Q = __uint2float_rn((uint32_t)Q1);
+    w.Qp = 2.0f;
+    w.soff = __fsub_rn(__uint2float_rn((uint32_t)s), kMagic);
+    w.sm = __fadd_rn(__uint2float_rn((uint32_t)s), kMagic);
+    w.acc2 = 2 * c1;
+    return false;
+}
+
+// One baby step j -> j+1.  Sets the two centre tests and t = 2*[P_{j+1} == 3
+// mod 4]; always advances the state and adds 2 log(P_{j+1}) = 2 + t to acc2.
+__device__ __forceinline__ void walk_step(WalkState &w, bool &centre_odd, bool &centre_even,
+                                          int &t) {
+    const float num = __fadd_rn(w.Pm, w.soff);                // P_j + s
+    const float rq = rcp_approx(w.Q);
+    const float qm = __fmaf_rd(num, rq, kMagic - 0.5f);       // 2^23 + (q or q-1)
+    float qf = __fsub_rn(qm, kMagic);
+    float r = __fmaf_rn(-qf, w.Q, num);                       // remainder, in [0, 2Q)
+    const float c = (r >= w.Q) ? 1.0f : 0.0f;
+    r = __fmaf_rn(-c, w.Q, r);
+    qf = __fadd_rn(qf, c);                                    // q_j
+    const float Pn = __fsub_rn(w.sm, r);                      // P_{j+1} + 2^23 = s - r + 2^23
+    const float dP = __fsub_rn(w.Pm, Pn);                     // P_j - P_{j+1}
+    const float Qn = __fmaf_rn(qf, dP, w.Qp);                 // Q_{j+1}
+    t = __float_as_int(Pn) & 2;
+    centre_odd = (Qn == w.Q);
+    centre_even = (dP == 0.0f);
+    w.acc2 += 2 + t;
+    w.Qp = w.Q;
+    w.Q = Qn;
+    w.Pm = Pn;
+}
+
+// log eps_d (mod 3, in 0..2) at the centre found by the last walk_step.
+__device__ __forceinline__ int walk_finish(const WalkState &w, bool centre_odd, int t) {
+    const int g = centre_odd ? (w.acc2 - 1 - (t >> 1)) : (w.acc2 - 2 - t);
+    return g % 3;
+}
+
+// Candidate index -> d by binary search over Segs sorted by cand0.
+__device__ __forceinline__ uint64_t cand_to_d(const Seg *__restrict__ segs, uint32_t nseg,
+                                              uint64_t cand) {
+    uint32_t lo = 0, hi = nseg;  // find the last seg with cand0 <= cand
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (segs[mid].cand0 <= cand) lo = mid; else hi = mid;
+    }
+    return segs[lo].d0 + 8 * (cand - segs[lo].cand0);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace eis

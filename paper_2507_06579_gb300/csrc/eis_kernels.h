@@ -1,0 +1,33 @@
+// eis_kernels.h -- kernel declarations shared by the .cu files of the library
+// (internal; the public boundary is include/eis.h).
+#pragma once
+
+#include <cstdint>
+
+#include "eis_common.cuh"
+
+namespace eis {
+
+__global__ void k_sieve(const Tile *tiles, const Seg *segs, const uint32_t *primes,
+                        uint32_t nprimes, uint32_t *sqfree, uint32_t *tile_pop);
+__global__ void k_scan_tiles(const uint32_t *tile_pop, uint32_t *tile_off, uint32_t ntiles,
+                             uint32_t *total);
+__global__ void k_compact(const Tile *tiles, const uint32_t *sqfree, const uint32_t *tile_off,
+                          uint32_t *surv);
+__global__ void k_count(const Tile *tiles, const uint32_t *flags, const uint32_t *sqfree,
+                        unsigned long long *counts);
+__global__ void k_expand_codes(const uint32_t *flags, const uint32_t *sqfree, uint64_t ncand,
+                               uint8_t *codes);
+__global__ void k_fill(uint32_t *buf, uint64_t nwords, uint32_t v);
+
+__global__ void k_walk_plain(uint64_t d_first, uint64_t cand_first, uint32_t ncand,
+                             const uint32_t *sqfree, uint32_t *flags, uint8_t *glog,
+                             unsigned long long *steps_acc, int *status, uint32_t step_limit);
+__global__ void k_walk_persistent(const Seg *segs, uint32_t nseg, const uint32_t *surv,
+                                  const uint32_t *n_surv_ptr, uint32_t *next_ptr, uint32_t *flags,
+                                  uint8_t *glog, unsigned long long *steps_acc, int *status,
+                                  uint32_t step_limit);
+__global__ void k_walk_single(uint64_t d, const uint32_t *primes, uint32_t nprimes, int *out,
+                              int *status, uint32_t step_limit);
+
+}  // namespace eis

@@ -1,0 +1,221 @@
+// k_sieve.cu -- candidate sieve, survivor compaction and counting kernels.
+//
+// Candidates are d == 5 (mod 8) (Section 1: D = { d == 5 mod 8, square-free }).
+// Such d are odd, so d is square-free iff no odd prime square p^2 divides it.
+// For odd p, p^2 == 1 (mod 8), hence the candidates divisible by p^2 are
+// exactly d = p^2 m with m == 5 (mod 8): consecutive hits are 8 p^2 apart in
+// d, p^2 apart in candidate index.  Each CTA sieves one tile of 2^16
+// candidates in shared memory (8 KB bitmap) and writes it to HBM once.
+#include "eis_common.cuh"
+#include "eis_kernels.h"
+
+namespace eis {
+
+namespace {
+
+// Primes whose hits per tile exceed this many are sieved by the whole CTA,
+// larger ones by one thread each.
+constexpr uint32_t kCoopP2 = 4096;
+
+__device__ __forceinline__ void clear_bit(uint32_t *bits, uint32_t idx) {
+    atomicAnd(&bits[idx >> 5], ~(1u << (idx & 31)));
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    uint32_t s = 0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// Exclusive block scan of one value per thread; returns the prefix and
+// writes the block total to *total (all threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *red, uint32_t *total) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (l >= o) x += y;
+    }
+    __syncthreads();
+    if (l == 31) red[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (l < nw) ? red[l] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (l >= o) s += y;
+        }
+        if (l < nw) red[l] = s;  // inclusive scan of warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_prefix = (w > 0) ? red[w - 1] : 0;
+    *total = red[nw - 1];
+    return warp_prefix + x - v;
+}
+
+}  // namespace
+
+// K1: one CTA per tile.  sqfree bit k = [candidate k is square-free];
+// tile_pop[t] = number of square-free candidates of tile t.
+__global__ void __launch_bounds__(256) k_sieve(const Tile *__restrict__ tiles,
+                                               const Seg *__restrict__ segs,
+                                               const uint32_t *__restrict__ primes,
+                                               uint32_t nprimes, uint32_t *__restrict__ sqfree,
+                                               uint32_t *__restrict__ tile_pop) {
+    __shared__ uint32_t bits[kTileWords];
+    __shared__ uint32_t red[32];
+    const Tile t = tiles[blockIdx.x];
+    const Seg s = segs[t.seg];
+    const uint64_t dfirst = s.d0 + 8 * (t.cand0 - s.cand0);
+    const uint64_t dlast = dfirst + 8 * (uint64_t)(t.ncand - 1);
+    const uint32_t nw = (t.ncand + 31) >> 5;
+    for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) {
+        uint32_t v = 0;
+        if (w < nw) {
+            const uint32_t rem = t.ncand - w * 32;
+            v = rem >= 32 ? kFull : ((1u << rem) - 1);
+        }
+        bits[w] = v;
+    }
+    __syncthreads();
+    // Small primes: the whole CTA strides over the hits of one prime.
+    uint32_t i = 0;
+    for (; i < nprimes; ++i) {
+        const uint64_t p = primes[i];
+        const uint64_t p2 = p * p;
+        if (p2 >= kCoopP2 || p2 > dlast) break;
+        uint64_t m = (dfirst + p2 - 1) / p2;
+        m += (13 - m % 8) % 8;  // m == 5 (mod 8)
+        const uint64_t dh = m * p2;
+        if (dh > dlast) continue;
+        const uint32_t first = (uint32_t)((dh - dfirst) >> 3);
+        const uint32_t nh = (uint32_t)((dlast - dh) / (8 * p2)) + 1;
+        for (uint32_t h = threadIdx.x; h < nh; h += blockDim.x)
+            clear_bit(bits, first + h * (uint32_t)p2);
+    }
+    // Larger primes: one thread per prime.
+    for (uint32_t j = i + threadIdx.x; j < nprimes; j += blockDim.x) {
+        const uint64_t p = primes[j];
+        const uint64_t p2 = p * p;
+        if (p2 > dlast) break;
+        uint64_t m = (dfirst + p2 - 1) / p2;
+        m += (13 - m % 8) % 8;
+        for (uint64_t dh = m * p2; dh <= dlast; dh += 8 * p2)
+            clear_bit(bits, (uint32_t)((dh - dfirst) >> 3));
+    }
+    __syncthreads();
+    uint32_t pop = 0;
+    const uint64_t wbase = t.cand0 >> 5;
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
+        const uint32_t v = bits[w];
+        sqfree[wbase + w] = v;
+        pop += __popc(v);
+    }
+    pop = block_sum(pop, red);
+    if (threadIdx.x == 0) tile_pop[blockIdx.x] = pop;
+}
+
+// Exclusive scan of tile_pop into tile_off (single CTA) and the total.
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict__ tile_pop,
+                                                     uint32_t *__restrict__ tile_off,
+                                                     uint32_t ntiles, uint32_t *__restrict__ total) {
+    __shared__ uint32_t red[32];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < ntiles ? tile_pop[i] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(v, red, &tot);
+        if (i < ntiles) tile_off[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Survivor queue: the global indices of the square-free candidates, tile by
+// tile in increasing order.  8 bitmap words per thread (256 threads = 2048
+// words = one tile).
+__global__ void __launch_bounds__(256) k_compact(const Tile *__restrict__ tiles,
+                                                 const uint32_t *__restrict__ sqfree,
+                                                 const uint32_t *__restrict__ tile_off,
+                                                 uint32_t *__restrict__ surv) {
+    __shared__ uint32_t red[32];
+    const Tile t = tiles[blockIdx.x];
+    const uint32_t nw = (t.ncand + 31) >> 5;
+    const uint64_t wbase = t.cand0 >> 5;
+    constexpr uint32_t kPer = kTileWords / 256;
+    uint32_t v[kPer];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const uint32_t w = threadIdx.x * kPer + k;
+        v[k] = (w < nw) ? sqfree[wbase + w] : 0u;
+        cnt += __popc(v[k]);
+    }
+    uint32_t tot;
+    uint32_t out = tile_off[blockIdx.x] + block_excl_scan(cnt, red, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        uint32_t x = v[k];
+        const uint32_t cbase = (uint32_t)(t.cand0 + 32u * (threadIdx.x * kPer + k));
+        while (x) {
+            const int b = __ffs(x) - 1;
+            surv[out++] = cbase + (uint32_t)b;
+            x &= x - 1;
+        }
+    }
+}
+
+// K4: per-interval counts.  counts[2*seg] += #E, counts[2*seg+1] += #D over
+// the tile's words (ballot/popcount data already packed in the bitmaps).
+__global__ void __launch_bounds__(256) k_count(const Tile *__restrict__ tiles,
+                                               const uint32_t *__restrict__ flags,
+                                               const uint32_t *__restrict__ sqfree,
+                                               unsigned long long *__restrict__ counts) {
+    __shared__ uint32_t red[32];
+    const Tile t = tiles[blockIdx.x];
+    const uint32_t nw = (t.ncand + 31) >> 5;
+    const uint64_t wbase = t.cand0 >> 5;
+    uint32_t e = 0, dd = 0;
+    for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
+        e += __popc(flags[wbase + w]);
+        dd += __popc(sqfree[wbase + w]);
+    }
+    e = block_sum(e, red);
+    __syncthreads();
+    dd = block_sum(dd, red);
+    if (threadIdx.x == 0) {
+        atomicAdd(&counts[2 * t.seg], (unsigned long long)e);
+        atomicAdd(&counts[2 * t.seg + 1], (unsigned long long)dd);
+    }
+}
+
+// Byte codes per candidate: 0 = not in D, 1 = in D \ E, 2 = in E.
+__global__ void __launch_bounds__(256) k_expand_codes(const uint32_t *__restrict__ flags,
+                                                      const uint32_t *__restrict__ sqfree,
+                                                      uint64_t ncand, uint8_t *__restrict__ codes) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < ncand;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = 1u << (k & 31);
+        const uint32_t sq = sqfree[k >> 5] & b, fl = flags[k >> 5] & b;
+        codes[k] = fl ? 2 : (sq ? 1 : 0);
+    }
+}
+
+// L2 flush helper for benchmarks: overwrite a buffer larger than L2.
+__global__ void k_fill(uint32_t *__restrict__ buf, uint64_t nwords, uint32_t v) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < nwords;
+         k += (uint64_t)gridDim.x * blockDim.x)
+        buf[k] = v;
+}
+
+}  // namespace eis

@@ -1,0 +1,186 @@
+// k_walk.cu -- the baby-step kernels (Appendix A walk, generator in Z/3).
+//
+//  k_walk_plain       one thread per candidate of a 2^24-wide block of d; the
+//                     flags of a warp's 32 consecutive candidates are one
+//                     ballot word.  A warp lasts as long as its longest walk.
+//  k_walk_persistent  one resident grid; every lane walks one d at a time and,
+//                     when its walk ends, takes the next square-free
+//                     candidate from a global queue (warp-aggregated atomic),
+//                     so lanes stay busy whatever the spread of periods.
+//  k_walk_single      one warp: square-free test of one d against the prime
+//                     table, then the walk in lane 0.
+#include "eis_common.cuh"
+#include "eis_kernels.h"
+
+namespace eis {
+
+__device__ __forceinline__ void record_result(uint32_t *__restrict__ flags,
+                                              uint8_t *__restrict__ glog, uint64_t cand, int g) {
+    if (g == 0) atomicOr(&flags[cand >> 5], 1u << (cand & 31));
+    if (glog) glog[cand] = (uint8_t)(1 + g);
+}
+
+__device__ __forceinline__ void add_steps(unsigned long long *acc, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+// K2.  Candidates [cand_first, cand_first + ncand) of one Seg, d of the first
+// one = d_first.  cand_first is a multiple of 32, so each warp owns whole
+// flag words and writes them without atomics.
+__global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t cand_first,
+                                                    uint32_t ncand,
+                                                    const uint32_t *__restrict__ sqfree,
+                                                    uint32_t *__restrict__ flags,
+                                                    uint8_t *__restrict__ glog,
+                                                    unsigned long long *__restrict__ steps_acc,
+                                                    int *__restrict__ status, uint32_t step_limit) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t cand = cand_first + i;
+    const bool valid = i < ncand;
+    bool inE = false;
+    unsigned long long steps = 0;
+    if (valid && ((sqfree[cand >> 5] >> (cand & 31)) & 1u)) {
+        const uint64_t d = d_first + 8ull * i;
+        WalkState w;
+        int g;
+        steps = 1;
+        if (!walk_init(d, w, g)) {
+            bool odd, even;
+            int t;
+            uint32_t n = 0;
+            do {
+                walk_step(w, odd, even, t);
+                ++n;
+            } while (!(odd || even) && n < step_limit);
+            steps += n;
+            if (odd || even) {
+                g = walk_finish(w, odd, t);
+            } else {
+                atomicOr(status, kErrSteps);
+                g = -1;
+            }
+        }
+        inE = (g == 0);
+        if (glog && g >= 0) glog[cand] = (uint8_t)(1 + g);
+    }
+    const uint32_t word = __ballot_sync(kFull, inE);
+    if ((threadIdx.x & 31) == 0 && valid) flags[cand >> 5] = word;
+    add_steps(steps_acc, steps);
+}
+
+// K5.  The survivor queue surv[0, *n_surv) holds global candidate indices in
+// increasing order; lanes take them from the end (largest d first within the
+// Seg layout, which is sorted by d0) so that the cheapest walks run last.
+__global__ void __launch_bounds__(256) k_walk_persistent(
+    const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
+    const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
+    uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
+    unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit) {
+    const uint32_t n_surv = *n_surv_ptr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    WalkState w;
+    walk_park(w);
+    bool active = false;
+    bool exhausted = false;  // warp-uniform
+    uint32_t cand = 0;
+    uint32_t done = 0;       // steps walked by the current d
+    unsigned long long my_steps = 0;
+    for (;;) {
+        // Refill idle lanes; repeat while fresh d end at the first step.
+        for (;;) {
+            const unsigned need = __ballot_sync(kFull, !active);
+            if (need == 0 || exhausted) break;
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(next_ptr, (uint32_t)__popc(need));
+            base = __shfl_sync(kFull, base, leader);
+            if ((uint64_t)base + __popc(need) >= n_surv) exhausted = true;
+            if (!active) {
+                const uint32_t idx = base + __popc(need & lt);
+                if (idx < n_surv) {
+                    cand = surv[n_surv - 1 - idx];
+                    const uint64_t d = cand_to_d(segs, nseg, cand);
+                    int g;
+                    my_steps += 1;
+                    if (walk_init(d, w, g)) {
+                        record_result(flags, glog, cand, g);
+                    } else {
+                        active = true;
+                        done = 0;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) break;
+        // Walk until some lane reaches its centre (or the step limit).
+        uint32_t room = active ? step_limit - done : 0xffffffffu;
+        for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
+        bool odd, even, ex;
+        int t;
+        uint32_t n = 0;
+        do {
+            walk_step(w, odd, even, t);
+            ++n;
+            ex = active && (odd || even);
+        } while (!__any_sync(kFull, ex) && n < room);
+        if (active) {
+            done += n;
+            if (ex) {
+                record_result(flags, glog, cand, walk_finish(w, odd, t));
+                my_steps += done;
+                active = false;
+            } else if (done >= step_limit) {
+                atomicOr(status, kErrSteps);
+                my_steps += done;
+                active = false;
+            }
+        }
+    }
+    add_steps(steps_acc, my_steps);
+}
+
+// Membership query for one d (one warp).  out[0] = 0 (d not in D) or
+// 1 + log eps_d; out[1] = steps.  The square-free test covers every odd prime
+// p with p^2 <= d from the table (d < 2^44 needs p < 2^22).
+__global__ void __launch_bounds__(32) k_walk_single(uint64_t d, const uint32_t *__restrict__ primes,
+                                                    uint32_t nprimes, int *__restrict__ out,
+                                                    int *__restrict__ status, uint32_t step_limit) {
+    bool hit = false;
+    for (uint32_t i = threadIdx.x; i < nprimes; i += 32) {
+        const uint64_t p = primes[i];
+        if (p * p > d) break;
+        if (d % (p * p) == 0) hit = true;
+    }
+    const bool sq = !__any_sync(kFull, hit);
+    if (threadIdx.x != 0) return;
+    if (!sq || d % 8 != 5) {
+        out[0] = 0;
+        out[1] = 0;
+        return;
+    }
+    WalkState w;
+    int g;
+    uint32_t n = 1;
+    if (!walk_init(d, w, g)) {
+        bool odd, even;
+        int t;
+        uint32_t k = 0;
+        do {
+            walk_step(w, odd, even, t);
+            ++k;
+        } while (!(odd || even) && k < step_limit);
+        n += k;
+        if (odd || even) {
+            g = walk_finish(w, odd, t);
+        } else {
+            atomicOr(status, kErrSteps);
+            g = -1;
+        }
+    }
+    out[0] = 1 + g;
+    out[1] = (int)n;
+}
+
+}  // namespace eis
