@@ -51,6 +51,8 @@ extern "C" {
 #define EIS_ESTEPS -7    /* a walk ran past its step limit (never expected) */
 #define EIS_EBUSY -8     /* serving: request not admitted (queue or memory full) */
 #define EIS_ENOTFOUND -9 /* serving: unknown request id */
+#define EIS_ETOOLARGE -10 /* eis_classify_range_noalloc: more candidates than its */
+                          /* fixed scratch holds (EIS_NOALLOC_MAX_CANDIDATES)      */
 
 /* Exclusive upper bound on hi (and on d): 2^44.  Below it every baby-step
  * quantity (P, Q, P + floor(sqrt d)) is an integer below 2^23, which the
@@ -160,6 +162,43 @@ int eis_is_eisenstein(eis_ctx *ctx, uint64_t d, int *result_out);
  * in one plan (one persistent launch). */
 int eis_count_batch(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t n,
                     uint64_t *counts_out);
+
+/* ---------------------------------------------------------------------
+ * Classification without device allocation
+ * ------------------------------------------------------------------- */
+
+/* Largest number of candidates (d == 5 mod 8) one call of
+ * eis_classify_range_noalloc accepts: 2^20, i.e. hi - lo <= 8 * 2^20. */
+#define EIS_NOALLOC_MAX_CANDIDATES (((uint64_t)1) << 20)
+
+/* The paper has no counterpart to this entry point: it exists for callers
+ * that must not allocate device memory -- code running inside a host
+ * callback or an allocator hook, a process whose GPU memory is owned by
+ * another framework's pool, or a real-time loop that forbids allocation after
+ * start-up.  Such callers cannot call eis_create (it allocates), so this call
+ * takes no context and calls no cudaMalloc, cudaFree or any allocating
+ * library routine.
+ *
+ * It classifies the candidates of [lo, hi) on `device` like
+ * eis_classify_range (same bit layout):
+ *   flags_out  : device pointer, ceil(n/32) words, bit = [d in E]   (required)
+ *   sqfree_out : device pointer, ceil(n/32) words, bit = [d in D]   (nullable)
+ *   count_out  : host pointer, #E cap [lo, hi)                      (nullable)
+ *   stream     : cudaStream_t, NULL for the legacy default stream
+ * It returns after the results are complete.  More than
+ * EIS_NOALLOC_MAX_CANDIDATES candidates give EIS_ETOOLARGE (nothing written);
+ * hi above EIS_D_LIMIT gives EIS_ERANGE.
+ *
+ * Its scratch (survivor queue, counters, a bitmap when sqfree_out is NULL,
+ * about 4.2 MB) is one fixed array in the library's device memory, which every
+ * GPU that loads the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (with the device made
+ * current); make that first call before any stream capture.  All calls share
+ * the array: the call clears what must start at zero, but two calls whose
+ * work overlaps on the GPU (other host threads, other streams) race on it,
+ * so issue them one after another. */
+int eis_classify_range_noalloc(int device, uint64_t lo, uint64_t hi, uint32_t *flags_out,
+                               uint32_t *sqfree_out, uint64_t *count_out, void *stream);
 
 /* ---------------------------------------------------------------------
  * Plans: device-resident, re-launchable pipelines over a fixed set of

@@ -41,6 +41,8 @@ EIS_EDEVICE = -6
 EIS_ESTEPS = -7
 EIS_EBUSY = -8
 EIS_ENOTFOUND = -9
+EIS_ETOOLARGE = -10
+EIS_NOALLOC_MAX_CANDIDATES = 1 << 20
 
 EIS_D_LIMIT = 1 << 44
 
@@ -102,6 +104,7 @@ SIGNATURES = [
     ("eis_classify_range_log", _I32, [_VP, _U64, _U64, _VP, _I32, _VP]),
     ("eis_is_eisenstein", _I32, [_VP, _U64, _P(_I32)]),
     ("eis_count_batch", _I32, [_VP, _VP, _VP, _SZ, _VP]),
+    ("eis_classify_range_noalloc", _I32, [_I32, _U64, _U64, _VP, _VP, _P(_U64), _VP]),
     ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
     ("eis_plan_launch", _I32, [_VP, _VP]),
     ("eis_plan_counts", _I32, [_VP, _VP]),

@@ -423,6 +423,7 @@ const char *eis_strerror(int code) {
         case EIS_ESTEPS: return "a walk ran past its step limit";
         case EIS_EBUSY: return "request not admitted";
         case EIS_ENOTFOUND: return "unknown request";
+        case EIS_ETOOLARGE: return "range has more candidates than the no-allocation call's fixed scratch (2^20)";
         default: return "unknown error";
     }
 }
