@@ -83,13 +83,15 @@ struct WalkState {
     int acc2;    // 2 S_j (sum of 2*log over the states walked), not reduced
 };
 
-// A benign valid state (d = 5 at j = 1): stepping it is a fixed point.
-__device__ __forceinline__ void walk_park(WalkState &w) {
-    w.Pm = kMagic + 1.0f;
-    w.Q = 2.0f;
-    w.Qp = 2.0f;
-    w.soff = 2.0f - kMagic;
-    w.sm = 2.0f + kMagic;
+// An idle state for lanes without a d: every quantity is NaN, so both centre
+// tests of walk_step compare false and the lane never reports a centre.
+__device__ __forceinline__ void walk_park_idle(WalkState &w) {
+    const float nan = __int_as_float(0x7fffffff);
+    w.Pm = nan;
+    w.Q = nan;
+    w.Qp = nan;
+    w.soff = nan;
+    w.sm = nan;
     w.acc2 = 0;
 }
 
@@ -115,33 +117,35 @@ __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
     return false;
 }
 
-// One baby step j -> j+1.  Sets the two centre tests and t = 2*[P_{j+1} == 3
-// mod 4]; always advances the state and adds 2 log(P_{j+1}) = 2 + t to acc2.
-__device__ __forceinline__ void walk_step(WalkState &w, bool &centre_odd, bool &centre_even,
-                                          int &t) {
+// One baby step j -> j+1.  Always advances the state and adds
+// 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2; returns true when the
+// new state is the centre of the period (Q_{j+1} = Q_j or P_{j+1} = P_j).
+__device__ __forceinline__ bool walk_step(WalkState &w) {
     const float num = __fadd_rn(w.Pm, w.soff);                // P_j + s
     const float rq = rcp_approx(w.Q);
     const float qm = __fmaf_rd(num, rq, kMagic - 0.5f);       // 2^23 + (q or q-1)
     float qf = __fsub_rn(qm, kMagic);
     float r = __fmaf_rn(-qf, w.Q, num);                       // remainder, in [0, 2Q)
-    const float c = (r >= w.Q) ? 1.0f : 0.0f;
-    r = __fmaf_rn(-c, w.Q, r);
-    qf = __fadd_rn(qf, c);                                    // q_j
+    if (r >= w.Q) {
+        r = __fsub_rn(r, w.Q);
+        qf = __fadd_rn(qf, 1.0f);                             // q_j
+    }
     const float Pn = __fsub_rn(w.sm, r);                      // P_{j+1} + 2^23 = s - r + 2^23
     const float dP = __fsub_rn(w.Pm, Pn);                     // P_j - P_{j+1}
     const float Qn = __fmaf_rn(qf, dP, w.Qp);                 // Q_{j+1}
-    t = __float_as_int(Pn) & 2;
-    centre_odd = (Qn == w.Q);
-    centre_even = (dP == 0.0f);
-    w.acc2 += 2 + t;
+    w.acc2 += 2 + (__float_as_int(Pn) & 2);
+    const bool centre = (Qn == w.Q) | (dP == 0.0f);
     w.Qp = w.Q;
     w.Q = Qn;
     w.Pm = Pn;
+    return centre;
 }
 
-// log eps_d (mod 3, in 0..2) at the centre found by the last walk_step.
-__device__ __forceinline__ int walk_finish(const WalkState &w, bool centre_odd, int t) {
-    const int g = centre_odd ? (w.acc2 - 1 - (t >> 1)) : (w.acc2 - 2 - t);
+// log eps_d (mod 3, in 0..2) once walk_step has returned true.  The centre
+// is of odd type (l = 2j+1) iff the last two Q are equal, else of even type.
+__device__ __forceinline__ int walk_finish(const WalkState &w) {
+    const int t = __float_as_int(w.Pm) & 2;
+    const int g = (w.Q == w.Qp) ? (w.acc2 - 1 - (t >> 1)) : (w.acc2 - 2 - t);
     return g % 3;
 }
 

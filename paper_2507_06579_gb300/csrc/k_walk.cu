@@ -46,16 +46,17 @@ __global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t c
         int g;
         steps = 1;
         if (!walk_init(d, w, g)) {
-            bool odd, even;
-            int t;
             uint32_t n = 0;
-            do {
-                walk_step(w, odd, even, t);
-                ++n;
-            } while (!(odd || even) && n < step_limit);
+            bool hit = false;
+            for (;;) {
+                if (walk_step(w)) { n += 1; hit = true; break; }
+                if (walk_step(w)) { n += 2; hit = true; break; }
+                n += 2;
+                if (n >= step_limit) break;
+            }
             steps += n;
-            if (odd || even) {
-                g = walk_finish(w, odd, t);
+            if (hit) {
+                g = walk_finish(w);
             } else {
                 atomicOr(status, kErrSteps);
                 g = -1;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     WalkState w;
-    walk_park(w);
+    walk_park_idle(w);
     bool active = false;
     bool exhausted = false;  // warp-uniform
     uint32_t cand = 0;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
                     my_steps += 1;
                     if (walk_init(d, w, g)) {
                         record_result(flags, glog, cand, g);
+                        walk_park_idle(w);
                     } else {
                         active = true;
                         done = 0;
@@ -114,27 +116,32 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
             }
         }
         if (!__any_sync(kFull, active)) break;
-        // Walk until some lane reaches its centre (or the step limit).
+        // Walk until some lane reaches its centre (or the step limit).  Idle
+        // lanes hold NaN states whose centre test is false.
         uint32_t room = active ? step_limit - done : 0xffffffffu;
         for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
-        bool odd, even, ex;
-        int t;
         uint32_t n = 0;
-        do {
-            walk_step(w, odd, even, t);
-            ++n;
-            ex = active && (odd || even);
-        } while (!__any_sync(kFull, ex) && n < room);
+        bool hit;
+        for (;;) {
+            hit = walk_step(w);
+            if (__any_sync(kFull, hit)) { n += 1; break; }
+            hit = walk_step(w);
+            if (__any_sync(kFull, hit)) { n += 2; break; }
+            n += 2;
+            if (n >= room) break;
+        }
         if (active) {
             done += n;
-            if (ex) {
-                record_result(flags, glog, cand, walk_finish(w, odd, t));
+            if (hit) {
+                record_result(flags, glog, cand, walk_finish(w));
                 my_steps += done;
                 active = false;
+                walk_park_idle(w);
             } else if (done >= step_limit) {
                 atomicOr(status, kErrSteps);
                 my_steps += done;
                 active = false;
+                walk_park_idle(w);
             }
         }
     }
@@ -164,16 +171,17 @@ __global__ void __launch_bounds__(32) k_walk_single(uint64_t d, const uint32_t *
     int g;
     uint32_t n = 1;
     if (!walk_init(d, w, g)) {
-        bool odd, even;
-        int t;
         uint32_t k = 0;
-        do {
-            walk_step(w, odd, even, t);
-            ++k;
-        } while (!(odd || even) && k < step_limit);
+        bool hit = false;
+        for (;;) {
+            if (walk_step(w)) { k += 1; hit = true; break; }
+            if (walk_step(w)) { k += 2; hit = true; break; }
+            k += 2;
+            if (k >= step_limit) break;
+        }
         n += k;
-        if (odd || even) {
-            g = walk_finish(w, odd, t);
+        if (hit) {
+            g = walk_finish(w);
         } else {
             atomicOr(status, kErrSteps);
             g = -1;
