@@ -129,7 +129,7 @@ def cpu_baseline(seconds_target: float = 12.0):
     import oracle
     oracle.build()
     cores = oracle.default_threads()
-    width = 8 * 2000
+    width = 8 * 4096 * cores  # at least one 4096-candidate block per core
     while True:
         lo, hi = TOP - width + 1, TOP + 1
         t0 = time.perf_counter()
@@ -138,7 +138,8 @@ def cpu_baseline(seconds_target: float = 12.0):
         if dt >= seconds_target / 2.5 or width >= 8 * 10**6:
             break
         width *= 4
-    return {"value": nD / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    used = min(cores, (width // 8 + 4095) // 4096)
+    return {"value": nD / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": "all candidates of [1e11-%d, 1e11] (%d discriminants, %.1f s, "
                       "full-period walk per d)" % (width - 1, nD, dt),
             "steps_per_s": steps / dt}
@@ -151,7 +152,9 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = oracle.default_threads()
-    width = 8 * 4000  # one step: ~4000 candidates at the top of the window
+    # one step: enough candidates that every core gets work (the oracle hands
+    # out blocks of 4096 candidates), about 4 blocks per core
+    width = 8 * 4096 * 4 * cores
     lo, hi = TOP - width + 1, TOP + 1
     for _ in range(args.warmup):
         oracle.count_range(lo, hi, cores)
@@ -186,6 +189,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=2,
+                    help="passes of the 4096-interval batched workload (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="seconds of Poisson arrivals per serving rate (0: skip)")
     ap.add_argument("--window", type=float, default=WINDOW,
                     help="per-rank window width below 1e11 (smaller for profiling runs)")
     args = ap.parse_args()
@@ -195,6 +202,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
+    import numpy as np
     import torch
     import paper_2507_06579_gb300 as E
 
@@ -265,6 +273,66 @@ def main():
                  "launches_per_step": psts[0]["launches"], "steps": args.plain_steps}
         pplan.destroy()
 
+    # batched uneven ranges: 4096 seeded intervals in one persistent launch,
+    # against the same intervals through the plain kernel
+    batched = None
+    if args.batched_steps > 0 and rank == 0:
+        from paper_2507_06579_gb300 import workloads as W
+        blo, bhi = W.batched_intervals(n=4096, seed=4)
+        res = {}
+        for name, mode in (("persistent", E.EIS_MODE_PERSISTENT), ("plain", E.EIS_MODE_PLAIN)):
+            bp = ctx.plan_create(blo, bhi, mode)
+            one(bp)
+            bsts = [one(bp) for _ in range(args.batched_steps)]
+            res[name] = {"ms_per_step": sum(s["ms_total"] for s in bsts) / len(bsts),
+                         "counts": bp.counts(), "in_D": bsts[0]["in_D"],
+                         "launches": bsts[0]["launches"], "steps": bsts[0]["baby_steps"]}
+            bp.destroy()
+        assert (res["persistent"]["counts"] == res["plain"]["counts"]).all()
+        bd = res["persistent"]["in_D"]
+        batched = {"workload": "4096 intervals [a, a+L), a log-uniform in [1e6, 1e12], "
+                               "L log-uniform in [1e3, 1e7], seed 4",
+                   "discriminants_per_step": bd,
+                   "baby_steps_per_step": res["persistent"]["steps"],
+                   "persistent": {"value": bd / (res["persistent"]["ms_per_step"] / 1e3),
+                                  "ms_per_step": res["persistent"]["ms_per_step"],
+                                  "launches_per_step": res["persistent"]["launches"]},
+                   "plain": {"value": bd / (res["plain"]["ms_per_step"] / 1e3),
+                             "ms_per_step": res["plain"]["ms_per_step"],
+                             "launches_per_step": res["plain"]["launches"]},
+                   "speedup": res["plain"]["ms_per_step"] / res["persistent"]["ms_per_step"],
+                   "sum_counts": int(res["persistent"]["counts"].sum())}
+
+    # serving: Poisson arrivals of range counts (90%) and membership queries
+    # (10%), replayed by a native client against the continuous-batching server
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        from paper_2507_06579_gb300 import workloads as W
+        rates = []
+        with E.Server(ctx) as srv:
+            for rate in (10.0, 100.0, 1000.0, 10000.0):
+                n = int(min(max(rate * args.serve_seconds, 20), 30000))
+                reqs = W.serving_stream(n, rate, seed=5)
+                out = srv.replay([r[0] for r in reqs],
+                                 [E.EIS_REQ_MEMBER if r[1] == "member" else E.EIS_REQ_COUNT
+                                  for r in reqs],
+                                 [r[2] for r in reqs], [r[3] for r in reqs])
+                lat = out["latency_us"] / 1e3
+                ok = (out["status"] == E.EIS_OK) | (out["status"] == E.EIS_ENOTD)
+                rates.append({"rate_rps": rate, "requests": n, "ok": int(ok.sum()),
+                              "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99)),
+                              "max_ms": float(lat.max()),
+                              "throughput_rps": n / out["wall_s"], "wall_s": out["wall_s"]})
+            sst = srv.stats()
+        serving = {"workload": "Poisson arrivals, 90% counts [a, a+L) with a log-uniform in "
+                               "[1e6, 1e12], L log-uniform in [1e2, 1e6]; 10% membership "
+                               "queries on d == 5 mod 8 below 1e12 (not-square-free d answer "
+                               "EIS_ENOTD); seed 5",
+                   "server": "4 slots x 2^22 candidates, continuous batching",
+                   "rates": rates, "batches": sst["batches"],
+                   "max_batch_parts": sst["max_batch_parts"]}
+
     # end to end through the public call with host buffers
     n_cand, _ = E.num_candidates(lo, hi)
     nw = (n_cand + 31) // 32
@@ -315,6 +383,8 @@ def main():
                            "parallelism": "dp%d (independent windows)" % world},
                 "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "batched": batched,
+                "serving": serving,
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": launches, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)

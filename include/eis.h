@@ -53,6 +53,7 @@ extern "C" {
 #define EIS_ENOTFOUND -9 /* serving: unknown request id */
 #define EIS_ETOOLARGE -10 /* eis_classify_range_noalloc: more candidates than its */
                           /* fixed scratch holds (EIS_NOALLOC_MAX_CANDIDATES)      */
+#define EIS_ECANCELED -11 /* serving: the request was cancelled                    */
 
 /* Exclusive upper bound on hi (and on d): 2^44.  Below it every baby-step
  * quantity (P, Q, P + floor(sqrt d)) is an integer below 2^23, which the
@@ -224,10 +225,86 @@ int eis_plan_counts(eis_plan *plan, uint64_t *counts_out);
 int eis_plan_bitmaps(eis_plan *plan, const uint32_t **flags, const uint32_t **sqfree,
                      uint64_t *word_offset, uint64_t *total_words);
 
+/* Wait for the last launch and copy the plan's bitmaps (total_words words
+ * each, layout as eis_plan_bitmaps) to caller memory: host pointers if
+ * out_on_device is 0, device pointers otherwise.  Either may be NULL. */
+int eis_plan_copy_bitmaps(eis_plan *plan, uint32_t *flags_out, uint32_t *sqfree_out,
+                          int out_on_device);
+
 /* Wait for the last launch and fill `out` (device times from CUDA events). */
 int eis_plan_stats(eis_plan *plan, eis_stats *out);
 
 int eis_plan_destroy(eis_plan *plan);
+
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of range counts and membership queries
+ * ------------------------------------------------------------------- */
+
+#define EIS_REQ_COUNT 0  /* #E cap [lo, hi) */
+#define EIS_REQ_MEMBER 1 /* is d = lo in E (result 1/0; EIS_ENOTD if d is not in D) */
+
+typedef struct eis_server eis_server;
+
+typedef struct {
+    uint32_t slots;           /* batches in flight at once, one stream each (4)  */
+    uint64_t slot_candidates; /* candidates one batch holds (2^22); larger       */
+                              /* requests are split into parts                   */
+    uint32_t slot_requests;   /* request parts one batch holds (4096)            */
+    uint32_t max_pending;     /* queued parts before submit refuses (2^20)       */
+} eis_server_config;
+
+typedef struct {
+    uint64_t requests_submitted;
+    uint64_t requests_done;
+    uint64_t rejected;        /* submits refused with EIS_EBUSY */
+    uint64_t batches;
+    uint64_t parts;
+    uint64_t max_batch_parts;
+    uint64_t pending_parts;
+    uint64_t reserved_bytes;  /* device memory of the slots */
+} eis_server_counters;
+
+/* Start a server on ctx's device.  Device memory for `slots` batches is
+ * allocated here and charged to the context budget (EIS_ENOMEM if it does not
+ * fit); a dispatcher thread then packs queued requests into whichever slot is
+ * free, so batches overlap on the device while new requests queue.  cfg may
+ * be NULL (defaults in the struct comments).  The context must outlive the
+ * server and must not be destroyed while it runs. */
+int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **out);
+
+/* Queue a request (kind EIS_REQ_COUNT: [lo, hi); EIS_REQ_MEMBER: d = lo, hi
+ * ignored).  Returns at once with *id_out; EIS_EBUSY when the queue is full
+ * (nothing queued).  Thread-safe. */
+int eis_server_submit(eis_server *srv, int kind, uint64_t lo, uint64_t hi, uint64_t *id_out);
+
+/* *done_out = 1 once the request has finished. */
+int eis_server_poll(eis_server *srv, uint64_t id, int *done_out);
+
+/* Wait up to timeout_ms for a request.  On completion returns the request's
+ * status (EIS_OK, EIS_ENOTD for a member query on d not in D, EIS_ESTEPS,
+ * EIS_ECANCELED, EIS_EDEVICE), writes the result (#E, or 1/0 for a member
+ * query) and the latency from submit to completion in microseconds, and
+ * forgets the request.  EIS_ETIMEOUT leaves it queued. */
+int eis_server_wait(eis_server *srv, uint64_t id, double timeout_ms, uint64_t *result_out,
+                    double *latency_us_out);
+
+/* Cancel a request: parts not yet on the device are dropped; the request
+ * completes with EIS_ECANCELED. */
+int eis_server_cancel(eis_server *srv, uint64_t id);
+
+int eis_server_stats(eis_server *srv, eis_server_counters *out);
+
+/* Finish the work in flight and queued, stop the dispatcher, free the slots. */
+int eis_server_destroy(eis_server *srv);
+
+/* Load replay: a native client thread submits request i at t_arrival_s[i]
+ * seconds after the call starts (kind[i], lo[i], hi[i]); results_out[i],
+ * status_out[i] and latency_us_out[i] (completion minus scheduled arrival)
+ * are written for every request; *wall_s_out = total time.  Output arrays
+ * are nullable.  Returns EIS_OK or the first error other than EIS_ENOTD. */
+int eis_server_replay(eis_server *srv, size_t n, const double *t_arrival_s, const int *kind,
+                      const uint64_t *lo, const uint64_t *hi, uint64_t *results_out,
+                      int *status_out, double *latency_us_out, double *wall_s_out);
 
 #ifdef __cplusplus
 }

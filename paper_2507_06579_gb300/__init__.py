@@ -42,6 +42,9 @@ EIS_ESTEPS = -7
 EIS_EBUSY = -8
 EIS_ENOTFOUND = -9
 EIS_ETOOLARGE = -10
+EIS_ECANCELED = -11
+EIS_REQ_COUNT = 0
+EIS_REQ_MEMBER = 1
 EIS_NOALLOC_MAX_CANDIDATES = 1 << 20
 
 EIS_D_LIMIT = 1 << 44
@@ -87,6 +90,20 @@ def build(force: bool = False) -> str:
     return _build.build(force=force)
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("slot_candidates", ctypes.c_uint64),
+                ("slot_requests", ctypes.c_uint32), ("max_pending", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "requests_submitted", "requests_done", "rejected", "batches", "parts",
+        "max_batch_parts", "pending_parts", "reserved_bytes")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 # (name, restype, argtypes) of every exported symbol declared in include/eis.h
 _VP, _U64, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 _P = ctypes.POINTER
@@ -109,8 +126,18 @@ SIGNATURES = [
     ("eis_plan_launch", _I32, [_VP, _VP]),
     ("eis_plan_counts", _I32, [_VP, _VP]),
     ("eis_plan_bitmaps", _I32, [_VP, _P(_VP), _P(_VP), _VP, _P(_U64)]),
+    ("eis_plan_copy_bitmaps", _I32, [_VP, _VP, _VP, _I32]),
     ("eis_plan_stats", _I32, [_VP, _P(Stats)]),
     ("eis_plan_destroy", _I32, [_VP]),
+    ("eis_server_create", _I32, [_VP, _P(ServerConfig), _P(_VP)]),
+    ("eis_server_submit", _I32, [_VP, _I32, _U64, _U64, _P(_U64)]),
+    ("eis_server_poll", _I32, [_VP, _U64, _P(_I32)]),
+    ("eis_server_wait", _I32, [_VP, _U64, ctypes.c_double, _P(_U64), _P(ctypes.c_double)]),
+    ("eis_server_cancel", _I32, [_VP, _U64]),
+    ("eis_server_stats", _I32, [_VP, _P(ServerStats)]),
+    ("eis_server_destroy", _I32, [_VP]),
+    ("eis_server_replay", _I32, [_VP, _SZ, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                 _P(ctypes.c_double)]),
 ]
 
 
@@ -190,6 +217,15 @@ class Plan:
                                       off.ctypes.data, ctypes.byref(tot)), "eis_plan_bitmaps")
         return f.value, s.value, off[: self.n], int(tot.value)
 
+    def copy_bitmaps(self):
+        """Host copies (flags, sqfree) of the plan's bitmaps (uint32 words)."""
+        _, _, _, tot = self.bitmaps()
+        f = np.zeros(max(tot, 1), dtype=np.uint32)
+        s = np.zeros(max(tot, 1), dtype=np.uint32)
+        _check(lib().eis_plan_copy_bitmaps(self.handle, f.ctypes.data, s.ctypes.data, 0),
+               "eis_plan_copy_bitmaps")
+        return f[:tot], s[:tot]
+
     def destroy(self):
         if self.handle:
             lib().eis_plan_destroy(self.handle)
@@ -198,6 +234,86 @@ class Plan:
     def __del__(self):
         try:
             self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (eis_server_*)."""
+
+    def __init__(self, ctx: "Context", slots: int = 0, slot_candidates: int = 0,
+                 slot_requests: int = 0, max_pending: int = 0):
+        self.ctx = ctx
+        cfg = ServerConfig(slots, slot_candidates, slot_requests, max_pending)
+        h = ctypes.c_void_p()
+        _check(lib().eis_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)),
+               "eis_server_create")
+        self.handle = h
+
+    def submit_count(self, lo: int, hi: int) -> int:
+        rid = ctypes.c_uint64()
+        _check(lib().eis_server_submit(self.handle, EIS_REQ_COUNT, lo, hi, ctypes.byref(rid)),
+               "eis_server_submit")
+        return int(rid.value)
+
+    def submit_member(self, d: int) -> int:
+        rid = ctypes.c_uint64()
+        _check(lib().eis_server_submit(self.handle, EIS_REQ_MEMBER, d, d + 1, ctypes.byref(rid)),
+               "eis_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int()
+        _check(lib().eis_server_poll(self.handle, rid, ctypes.byref(done)), "eis_server_poll")
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: float = 60_000.0):
+        """(status, result, latency_us); status is an EIS_* code (EIS_ETIMEOUT
+        leaves the request queued)."""
+        res = ctypes.c_uint64()
+        lat = ctypes.c_double()
+        rc = lib().eis_server_wait(self.handle, rid, timeout_ms, ctypes.byref(res), ctypes.byref(lat))
+        return rc, int(res.value), float(lat.value)
+
+    def cancel(self, rid: int):
+        _check(lib().eis_server_cancel(self.handle, rid), "eis_server_cancel")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().eis_server_stats(self.handle, ctypes.byref(st)), "eis_server_stats")
+        return st.as_dict()
+
+    def replay(self, t_arrival_s, kinds, los, his):
+        """Native load replay -> dict of numpy arrays (results, status,
+        latency_us) and the wall time."""
+        n = len(t_arrival_s)
+        t = np.ascontiguousarray(np.asarray(t_arrival_s, dtype=np.float64))
+        k = np.ascontiguousarray(np.asarray(kinds, dtype=np.int32))
+        lo, hi = _u64_array(los), _u64_array(his)
+        res = np.zeros(max(n, 1), dtype=np.uint64)
+        st = np.zeros(max(n, 1), dtype=np.int32)
+        lat = np.zeros(max(n, 1), dtype=np.float64)
+        wall = ctypes.c_double()
+        rc = lib().eis_server_replay(self.handle, n, t.ctypes.data, k.ctypes.data, lo.ctypes.data,
+                                     hi.ctypes.data, res.ctypes.data, st.ctypes.data,
+                                     lat.ctypes.data, ctypes.byref(wall))
+        return {"rc": rc, "results": res[:n], "status": st[:n], "latency_us": lat[:n],
+                "wall_s": float(wall.value)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().eis_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "eis.h"
+#include "eis_internal.h"
 #include "eis_kernels.h"
 
 using namespace eis;
@@ -407,6 +408,27 @@ static int run_chunks(eis_ctx *c, uint64_t lo, uint64_t hi, int with_log, cudaSt
     return EIS_OK;
 }
 
+// ------------------------------------------------------------------ internal view
+
+eis_ctx_view eis_ctx_get_view(eis_ctx *c) {
+    eis_ctx_view v;
+    v.device = c->device;
+    v.d_primes = c->d_primes;
+    v.nprimes = c->nprimes;
+    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : c->occ_persistent;
+    v.walk_grid = (uint32_t)(c->sm_count * std::max(1, per_sm));
+    v.step_limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
+    return v;
+}
+
+bool eis_ctx_reserve(eis_ctx *c, uint64_t bytes) {
+    if (c->in_use + bytes > c->budget) return false;
+    c->in_use += bytes;
+    return true;
+}
+
+void eis_ctx_release(eis_ctx *c, uint64_t bytes) { c->in_use -= std::min(c->in_use, bytes); }
+
 // ------------------------------------------------------------------ C-ABI
 
 extern "C" {
@@ -423,6 +445,7 @@ const char *eis_strerror(int code) {
         case EIS_ESTEPS: return "a walk ran past its step limit";
         case EIS_EBUSY: return "request not admitted";
         case EIS_ENOTFOUND: return "unknown request";
+        case EIS_ECANCELED: return "request cancelled";
         case EIS_ETOOLARGE: return "range has more candidates than the no-allocation call's fixed scratch (2^20)";
         default: return "unknown error";
     }
@@ -562,6 +585,17 @@ int eis_plan_bitmaps(eis_plan *p, const uint32_t **flags, const uint32_t **sqfre
     if (word_offset)
         for (size_t i = 0; i < p->n; ++i) word_offset[i] = p->word_off[i];
     if (total_words) *total_words = p->nwords;
+    return EIS_OK;
+}
+
+int eis_plan_copy_bitmaps(eis_plan *p, uint32_t *flags_out, uint32_t *sqfree_out,
+                          int out_on_device) {
+    if (!p) return EIS_EINVAL;
+    int rc = plan_wait(p);
+    if (rc != EIS_OK) return rc;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (flags_out && p->nwords) EIS_CK(cudaMemcpy(flags_out, p->d_flags, p->nwords * 4, kind));
+    if (sqfree_out && p->nwords) EIS_CK(cudaMemcpy(sqfree_out, p->d_sqfree, p->nwords * 4, kind));
     return EIS_OK;
 }
 

@@ -1,0 +1,20 @@
+// eis_internal.h -- what other translation units of the library may see of a
+// context (internal; the public boundary is include/eis.h).
+#pragma once
+
+#include <cstdint>
+
+#include "eis.h"
+
+struct eis_ctx_view {
+    int device;
+    const uint32_t *d_primes;  // odd primes < 2^22 on the device
+    uint32_t nprimes;
+    uint32_t walk_grid;        // persistent walk grid (SMs x resident CTAs)
+    uint32_t step_limit;
+};
+
+eis_ctx_view eis_ctx_get_view(eis_ctx *ctx);
+// Account `bytes` of device memory against the context budget; false if over.
+bool eis_ctx_reserve(eis_ctx *ctx, uint64_t bytes);
+void eis_ctx_release(eis_ctx *ctx, uint64_t bytes);

@@ -272,3 +272,42 @@ def test_full_1e9_config(ctx, orc):
         b = (iv["hi"] - d0 + 7) // 8
         assert _count_bits(f, a, b) == iv["total"]
     assert _count_bits(s, 0, n) == count_D_mobius(lo, hi)
+
+
+def test_full_batched_intervals(ctx, orc):
+    """4096 seeded intervals in one persistent launch == the same intervals
+    through the plain kernel; the cheapest intervals against the oracle; and
+    sampled candidates of the expensive ones against the oracle one by one."""
+    lo, hi = W.batched_intervals(n=4096, seed=4)
+    counts = {}
+    for mode in MODES:
+        plan = ctx.plan_create(lo, hi, mode)
+        plan.launch()
+        counts[mode] = plan.counts()
+        if mode == E.EIS_MODE_PERSISTENT:
+            _, _, off, _ = plan.bitmaps()
+            f_host, s_host = plan.copy_bitmaps()
+        plan.destroy()
+    assert np.array_equal(counts[E.EIS_MODE_PERSISTENT], counts[E.EIS_MODE_PLAIN])
+    # the cheapest intervals (work ~ L sqrt(a)) in full against the oracle
+    work = (hi - lo).astype(np.float64) * np.sqrt(lo.astype(np.float64))
+    for i in np.argsort(work)[:40]:
+        assert int(counts[E.EIS_MODE_PERSISTENT][i]) == orc.count_range(int(lo[i]), int(hi[i]))[1]
+    # sampled candidates of the most expensive intervals
+    rng = np.random.default_rng(5)
+    for i in np.argsort(work)[-8:]:
+        n, d0 = E.num_candidates(int(lo[i]), int(hi[i]))
+        ks = rng.choice(n, size=min(n, 20), replace=False)
+        ds = [d0 + 8 * int(k) for k in ks]
+        with cf.ThreadPoolExecutor(max_workers=orc.default_threads()) as ex:
+            res = list(ex.map(orc.walk_mod2, ds))
+        base = int(off[i]) * 32
+        for k, (rc, theta, _) in zip(ks, res):
+            g = base + int(k)
+            fbit = (int(f_host[g >> 5]) >> (g & 31)) & 1
+            sbit = (int(s_host[g >> 5]) >> (g & 31)) & 1
+            if rc == orc.ORC_ENOTD:
+                assert sbit == 0 and fbit == 0
+            else:
+                assert sbit == 1 and fbit == int(theta == 1)
+
