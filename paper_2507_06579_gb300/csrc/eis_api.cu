@@ -3,6 +3,7 @@
 // convenience calls.  All device memory of a pipeline is allocated when the
 // plan is created; eis_plan_launch only enqueues kernels (or one graph).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
@@ -38,6 +39,7 @@ struct eis_ctx {
     uint32_t *d_primes = nullptr;
     uint32_t nprimes = 0;
     int *d_single = nullptr;  // [0] result, [1] steps, [2] status
+    unsigned char *d_query = nullptr;  // K3 single query: u64 d, i8 out, int status, u64 acc[2], u32 next
     int mode = EIS_MODE_PERSISTENT;
     int ctas_per_sm = 0;
     int threads = 256;
@@ -73,12 +75,16 @@ struct eis_plan {
     unsigned long long *d_counts = nullptr;  // [2 s] #E, [2 s + 1] #D
     unsigned long long *d_steps = nullptr;   // [0] baby, [1] giant, [2] deferred
     uint8_t *d_glog = nullptr;
+    uint32_t *d_defer = nullptr;  // candidates handed to the giant-step kernel
+    uint32_t defer_cap = 0, defer_after = 0;
+    int giant_nbaby = 0, giant_log2n = 0;
+    uint32_t giant_grid = 0;
     uint64_t bytes = 0;
     uint32_t walk_grid = 0;
     int launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
     bool launched = false;
 };
@@ -124,6 +130,28 @@ static uint64_t max_chunk_cands(const eis_ctx *c, int with_log) {
     return m;
 }
 
+// Baby-step count N of the giant-step search for discriminants up to d: about
+// twice the square root of a typical period (~0.13 sqrt(d) steps), a power of
+// two in [256, 4096]; the table holds 4N entries (load <= 1/2).
+static void giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n) {
+    int n;
+    if (forced > 0) {
+        n = 256;
+        while (n < forced && n < 4096) n *= 2;
+    } else {
+        const double ell = 0.13 * std::sqrt((double)d);
+        const double want = 2.0 * std::sqrt(std::max(ell, 1.0));
+        n = 256;
+        while (n < want && n < 4096) n *= 2;
+    }
+    nbaby = n;
+    log2n = 2;
+    while ((1 << log2n) < 4 * n) ++log2n;
+}
+
+static constexpr int kGiantMaxLog2 = 14;  // 128 KB table per warp at most
+static constexpr uint32_t kGiantMaxRounds = 1u << 20;
+
 static void record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
     if (capturing)
         cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
@@ -153,11 +181,21 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
             k_compact<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_sqfree, p->d_tile_off, p->d_surv);
             launches += 2;
             record(p->ev[1], s, capturing);
-            k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(p->d_segs, nseg, p->d_surv, p->d_ctr,
-                                                           p->d_ctr + 1, p->d_flags, p->d_glog,
-                                                           p->d_steps, p->d_status, limit);
+            k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
+                p->d_segs, nseg, p->d_surv, p->d_ctr, p->d_ctr + 1, p->d_flags, p->d_glog,
+                p->d_steps, p->d_status, limit, p->defer_after, p->d_defer, p->d_ctr + 2,
+                p->defer_cap);
             ++launches;
             record(p->ev[2], s, capturing);
+            if (p->d_defer) {
+                const size_t smem = (size_t)8 << p->giant_log2n;
+                k_giant<<<p->giant_grid, 32, smem, s>>>(
+                    nullptr, p->d_segs, nseg, p->d_defer, p->d_ctr + 2, p->defer_cap,
+                    p->d_ctr + 3, c->d_primes, c->nprimes, nullptr, p->d_flags, p->d_glog,
+                    p->d_steps + 1, p->d_status, p->giant_nbaby, p->giant_log2n, kGiantMaxRounds);
+                ++launches;
+            }
+            record(p->ev[4], s, capturing);
         } else {
             record(p->ev[1], s, capturing);
             for (const PlainBlock &b : p->blocks) {
@@ -168,12 +206,14 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                 ++launches;
             }
             record(p->ev[2], s, capturing);
+            record(p->ev[4], s, capturing);
         }
         k_count<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_flags, p->d_sqfree, p->d_counts);
         ++launches;
     } else {
         record(p->ev[1], s, capturing);
         record(p->ev[2], s, capturing);
+        record(p->ev[4], s, capturing);
     }
     record(p->ev[3], s, capturing);
     EIS_CK(cudaGetLastError());
@@ -188,7 +228,8 @@ static void plan_free(eis_plan *p) {
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
     void *bufs[] = {p->d_segs, p->d_tiles, p->d_sqfree, p->d_flags, p->d_tile_pop, p->d_tile_off,
-                    p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog};
+                    p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog,
+                    p->d_defer};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->ctx) p->ctx->in_use -= std::min(p->ctx->in_use, p->bytes);
@@ -265,6 +306,23 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     EIS_ALLOC(p->d_counts, 2 * nseg * sizeof(unsigned long long) + 8);
     EIS_ALLOC(p->d_steps, 4 * sizeof(unsigned long long));
     if (with_log) EIS_ALLOC(p->d_glog, p->total_cand);
+    if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && p->total_cand > 0) {
+        uint64_t dmax = 0;
+        for (const Seg &sg : p->segs)
+            if (sg.ncand) dmax = std::max(dmax, sg.d0 + 8 * (sg.ncand - 1));
+        giant_params(dmax, c->giant_stride, p->giant_nbaby, p->giant_log2n);
+        p->giant_log2n = std::min(p->giant_log2n, kGiantMaxLog2);
+        p->defer_after = (uint32_t)std::min<int64_t>(c->giant_threshold, 0xffffffffll);
+        p->defer_cap = (uint32_t)std::min<uint64_t>(p->total_cand, std::max<uint64_t>(1u << 16, p->total_cand / 4));
+        EIS_ALLOC(p->d_defer, (size_t)p->defer_cap * 4);
+        int occ = 0;
+        const size_t smem = (size_t)8 << p->giant_log2n;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_giant, 32, smem) != cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        p->giant_grid = (uint32_t)(c->sm_count * std::max(1, occ));
+    }
 #undef EIS_ALLOC
     for (auto &e : p->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -325,7 +383,7 @@ static int plan_wait(eis_plan *p) {
     EIS_CK(cudaStreamSynchronize(p->last_stream));
     int status = 0;
     EIS_CK(cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (status & kErrSteps) return EIS_ESTEPS;
+    if (status & (kErrSteps | kErrGiant)) return EIS_ESTEPS;
     return EIS_OK;
 }
 
@@ -343,13 +401,16 @@ static int plan_fill_stats(eis_plan *p, eis_stats *st) {
         st->in_E += cnt[2 * i];
         st->in_D += cnt[2 * i + 1];
     }
-    st->baby_steps = steps[0];
-    st->giant_steps = steps[1];
-    st->deferred = steps[2];
+    st->baby_steps = steps[0] + steps[1];
+    st->giant_steps = steps[2];
+    uint32_t ctr[4] = {0, 0, 0, 0};
+    EIS_CK(cudaMemcpy(ctr, p->d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+    st->deferred = p->d_defer ? std::min(ctr[2], p->defer_cap) : 0;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[3]) == cudaSuccess) st->ms_total = ms;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) st->ms_sieve = ms;
     if (cudaEventElapsedTime(&ms, p->ev[1], p->ev[2]) == cudaSuccess) st->ms_walk = ms;
+    if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[4]) == cudaSuccess) st->ms_giant = ms;
     cudaGetLastError();
     st->launches = p->launches;
     st->sm_count = p->ctx->sm_count;
@@ -483,7 +544,16 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
         eis_destroy(c);
         return EIS_ENOMEM;
     }
-    c->in_use = pr.size() * 4 + 4 * sizeof(int);
+    if (cudaMalloc(&c->d_query, 64) != cudaSuccess) {
+        eis_destroy(c);
+        return EIS_ENOMEM;
+    }
+    c->in_use = pr.size() * 4 + 4 * sizeof(int) + 64;
+    if (cudaFuncSetAttribute(k_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8u << kGiantMaxLog2)) != cudaSuccess) {
+        eis_destroy(c);
+        return EIS_EDEVICE;
+    }
     if (cudaMemcpy(c->d_primes, pr.data(), pr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         eis_destroy(c);
         return EIS_EDEVICE;
@@ -502,6 +572,7 @@ int eis_destroy(eis_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->d_primes) cudaFree(c->d_primes);
     if (c->d_single) cudaFree(c->d_single);
+    if (c->d_query) cudaFree(c->d_query);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return EIS_OK;
@@ -703,21 +774,54 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
     if (d % 8 != 5) return EIS_ENOTD;
     EIS_CK(cudaSetDevice(c->device));
     const uint32_t limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
-    EIS_CK(cudaMemsetAsync(c->d_single, 0, 4 * sizeof(int), c->stream));
-    k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->nprimes, c->d_single,
-                                           c->d_single + 2, limit);
-    EIS_CK(cudaGetLastError());
-    int h[4] = {0, 0, 0, 0};
-    EIS_CK(cudaMemcpyAsync(h, c->d_single, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    EIS_CK(cudaStreamSynchronize(c->stream));
-    if (h[2] & kErrSteps) return EIS_ESTEPS;
     std::memset(&c->last, 0, sizeof(c->last));
     c->last.candidates = 1;
-    c->last.baby_steps = (uint64_t)h[1];
-    if (h[0] == 0) return EIS_ENOTD;
+    int res = 0;  // 0: not in D, else 1 + log eps_d
+    if (c->mode == EIS_MODE_PLAIN) {
+        // one lane walks the half period
+        EIS_CK(cudaMemsetAsync(c->d_single, 0, 4 * sizeof(int), c->stream));
+        k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->nprimes, c->d_single,
+                                               c->d_single + 2, limit);
+        EIS_CK(cudaGetLastError());
+        int h[4] = {0, 0, 0, 0};
+        EIS_CK(cudaMemcpyAsync(h, c->d_single, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        EIS_CK(cudaStreamSynchronize(c->stream));
+        if (h[2] & kErrSteps) return EIS_ESTEPS;
+        c->last.baby_steps = (uint64_t)h[1];
+        res = h[0];
+    } else {
+        // one warp: baby steps into a shared-memory table, 32 lanes of giant steps
+        int nbaby, log2n;
+        giant_params(d, c->giant_stride, nbaby, log2n);
+        log2n = std::min(log2n, kGiantMaxLog2);
+        unsigned char *q = c->d_query;  // [0] d, [8] out, [12] status, [16] acc[2], [32] next
+        EIS_CK(cudaMemsetAsync(q, 0, 64, c->stream));
+        EIS_CK(cudaMemcpyAsync(q, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
+        k_giant<<<1, 32, (size_t)8 << log2n, c->stream>>>(
+            reinterpret_cast<const uint64_t *>(q), nullptr, 0, nullptr, nullptr, 1,
+            reinterpret_cast<uint32_t *>(q + 32), c->d_primes, c->nprimes,
+            reinterpret_cast<int8_t *>(q + 8), nullptr, nullptr,
+            reinterpret_cast<unsigned long long *>(q + 16), reinterpret_cast<int *>(q + 12), nbaby,
+            log2n, kGiantMaxRounds);
+        EIS_CK(cudaGetLastError());
+        unsigned char h[64];
+        EIS_CK(cudaMemcpyAsync(h, q, 64, cudaMemcpyDeviceToHost, c->stream));
+        EIS_CK(cudaStreamSynchronize(c->stream));
+        int status = 0;
+        int8_t out = 0;
+        unsigned long long acc[2] = {0, 0};
+        std::memcpy(&out, h + 8, 1);
+        std::memcpy(&status, h + 12, sizeof(int));
+        std::memcpy(acc, h + 16, sizeof(acc));
+        if ((status & kErrGiant) || out < 0) return EIS_ESTEPS;
+        c->last.baby_steps = acc[0];
+        c->last.giant_steps = acc[1];
+        res = out;
+    }
+    if (res == 0) return EIS_ENOTD;
     c->last.in_D = 1;
-    c->last.in_E = (h[0] == 1);
-    *result_out = (h[0] == 1) ? 1 : 0;
+    c->last.in_E = (res == 1);
+    *result_out = (res == 1) ? 1 : 0;
     return EIS_OK;
 }
 

@@ -57,7 +57,8 @@ struct Tile {
 };
 
 // Error codes written by kernels into the plan's status word.
-constexpr int kErrSteps = 1;
+constexpr int kErrSteps = 1;  // a baby walk ran past its step limit
+constexpr int kErrGiant = 2;  // a giant-step search failed (table full, no hit)
 
 // floor(sqrt(d)) for d < 2^53: correctly rounded double sqrt, then exact
 // integer fix-ups (at most one step each way).

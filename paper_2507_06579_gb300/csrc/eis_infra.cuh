@@ -1,0 +1,202 @@
+// eis_infra.cuh -- infrastructure giant steps (Algorithm 1) with the
+// generator kept in (O_K/2O_K)* = Z/3 (Appendix A).
+//
+// An ideal is [a, (b + sqrt d)/2] with a = Q/2 > 0 odd and b odd, plus the
+// class g in Z/3 of the generator it was reached with.
+//
+// Composition: the product of two primitive ideals is e [a3, (b3+sqrt d)/2]
+// with e odd (it divides a1), so the primitive part's generator class is
+// g1 + g2.  (a3, b3) follow the textbook form-composition algorithm; every
+// product is reduced modulo v1 = a1/e first, so all values stay in int64 for
+// d < 2^44.
+//
+// Reduction applies rho (Appendix A) until the ideal is reduced:
+// q = floor((P + sqrt d)/Q) = floor((P + s)/Q) for Q > 0 and
+// floor((P + s + 1)/Q) for Q < 0 (s = floor(sqrt d)), P' = qQ - P,
+// Q' = (d - P'^2)/Q, and the class gains log((P'-1)/2 + omega) mod 2, which
+// is 1 when P' == 1 (mod 4) and 2 when P' == 3 (mod 4) (Q/2 odd, sign +-1
+// == 1 mod 2).  P'^2 can exceed 2^64 on the first steps, but |Q'| < 2^62, so
+// Q' is recovered exactly from d - P'^2 mod 2^64 by exact division: with
+// Q = 2a, ((d - P'^2) mod 2^64) >> 1 = a Q' (mod 2^63), times the inverse of
+// a modulo 2^64 (Newton iteration x <- x(2 - a x)).
+//
+// Reduced: Q > 0, 0 < P <= s and s - P < Q <= s + P (sqrt d irrational).
+#pragma once
+
+#include <cstdint>
+
+#include "eis_common.cuh"
+
+namespace eis {
+
+struct Ideal {
+    int64_t a;  // Q/2
+    int64_t b;  // P
+    int g;      // generator class in Z/3
+};
+
+// Extended Euclid: returns gcd(a, b) >= 0 with x a + y b = gcd.
+__device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t &x, int64_t &y) {
+    int64_t x0 = 1, y0 = 0, x1 = 0, y1 = 1;
+    while (b != 0) {
+        const int64_t q = a / b;
+        int64_t t = a - q * b;
+        a = b;
+        b = t;
+        t = x0 - q * x1;
+        x0 = x1;
+        x1 = t;
+        t = y0 - q * y1;
+        y0 = y1;
+        y1 = t;
+    }
+    if (a < 0) {
+        a = -a;
+        x0 = -x0;
+        y0 = -y0;
+    }
+    x = x0;
+    y = y0;
+    return a;
+}
+
+__device__ __forceinline__ int64_t mod_pos(int64_t x, int64_t m) {
+    int64_t r = x % m;
+    return r < 0 ? r + m : r;
+}
+
+__device__ __forceinline__ int64_t floor_div(int64_t x, int64_t y) {
+    int64_t q = x / y;
+    if ((x % y != 0) && ((x < 0) != (y < 0))) --q;
+    return q;
+}
+
+// Inverse of an odd a modulo 2^64.
+__device__ __forceinline__ uint64_t inv_odd_u64(uint64_t a) {
+    uint64_t x = a;  // a * a == 1 (mod 8): 3 correct bits
+#pragma unroll
+    for (int i = 0; i < 5; ++i) x *= 2 - a * x;
+    return x;
+}
+
+// Primitive part (a3, b3) of the product of [a1,(b1+sqrt d)/2] and
+// [a2,(b2+sqrt d)/2] (both primitive, b odd, 4a | b^2 - d, a < 2^22).
+__device__ __forceinline__ void ideal_compose(int64_t a1, int64_t b1, int64_t a2, int64_t b2,
+                                              int64_t d, int64_t &a3, int64_t &b3) {
+    if (a1 > a2) {
+        int64_t t = a1; a1 = a2; a2 = t;
+        t = b1; b1 = b2; b2 = t;
+    }
+    const int64_t s = (b1 + b2) / 2;
+    const int64_t n = b2 - s;
+    const int64_t c2 = (b2 * b2 - d) / (4 * a2);
+    int64_t y1, dd;
+    if (a2 % a1 == 0) {
+        y1 = 0;
+        dd = a1;
+    } else {
+        int64_t u, v;
+        dd = egcd64(a2, a1, u, v);  // u a2 + v a1 = dd
+        y1 = u;
+    }
+    int64_t x2, y2, d1;
+    if (s % dd == 0) {
+        y2 = -1;
+        x2 = 0;
+        d1 = dd;
+    } else {
+        int64_t u, v;
+        d1 = egcd64(s, dd, u, v);   // u s + v dd = d1
+        x2 = u;
+        y2 = -v;
+    }
+    const int64_t v1 = a1 / d1, v2 = a2 / d1;
+    int64_t r = 0;
+    if (v1 > 1) {
+        const int64_t t1 = mod_pos(mod_pos(y1, v1) * mod_pos(y2, v1), v1) * mod_pos(n, v1);
+        const int64_t t2 = mod_pos(x2, v1) * mod_pos(c2, v1);
+        r = mod_pos(mod_pos(t1, v1) - mod_pos(t2, v1), v1);
+    }
+    b3 = b2 + 2 * v2 * r;
+    a3 = v1 * v2;
+}
+
+__device__ __forceinline__ bool ideal_is_reduced(int64_t P, int64_t Q, int64_t s) {
+    return Q > 0 && P > 0 && P <= s && s - P < Q && Q <= s + P;
+}
+
+// rho until reduced; returns the class gained, or -1 past max_steps.
+__device__ __forceinline__ int ideal_reduce(int64_t &P, int64_t &Q, int64_t d, int64_t s,
+                                            int max_steps) {
+    int g = 0;
+    for (int it = 0; !ideal_is_reduced(P, Q, s); ++it) {
+        if (it >= max_steps) return -1;
+        const int64_t q = Q > 0 ? floor_div(P + s, Q) : floor_div(P + s + 1, Q);
+        const int64_t Pn = q * Q - P;
+        const uint64_t X = (uint64_t)d - (uint64_t)Pn * (uint64_t)Pn;  // d - P'^2 mod 2^64
+        const int64_t ha = Q > 0 ? Q / 2 : -(Q / 2);                    // |Q|/2, odd
+        const uint64_t m = ((X >> 1) * inv_odd_u64((uint64_t)ha)) & 0x7fffffffffffffffull;
+        int64_t Qn = (m & 0x4000000000000000ull) ? (int64_t)(m | 0x8000000000000000ull) : (int64_t)m;
+        if (Q < 0) Qn = -Qn;
+        g += 1 + (int)((Pn >> 1) & 1);
+        P = Pn;
+        Q = Qn;
+    }
+    return g;
+}
+
+// reduce(X * Y) with classes; returns false if the reduction ran away.
+__device__ __forceinline__ bool ideal_mul(const Ideal &X, const Ideal &Y, int64_t d, int64_t s,
+                                          Ideal &out) {
+    int64_t a3, b3;
+    ideal_compose(X.a, X.b, Y.a, Y.b, d, a3, b3);
+    int64_t P = b3, Q = 2 * a3;
+    const int gr = ideal_reduce(P, Q, d, s, 256);
+    if (gr < 0) return false;
+    out.a = Q / 2;
+    out.b = P;
+    out.g = (X.g + Y.g + gr) % 3;
+    return true;
+}
+
+// ---------------------------------------------------------------- baby table
+// Open-addressing hash in shared memory, one per warp, written by lane 0 only.
+// Entry: key (Q << 24 | P) << 3 | type << 2 | class, 0 = empty.
+constexpr uint64_t kMirror = 1;
+
+__device__ __forceinline__ uint64_t infra_key(int64_t Q, int64_t P) {
+    return ((uint64_t)Q << 24) | (uint64_t)P;
+}
+
+__device__ __forceinline__ uint32_t infra_hash(uint64_t key, int log2n) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2n));
+}
+
+__device__ __forceinline__ bool infra_insert(uint64_t *tab, int log2n, uint64_t key, uint64_t type,
+                                             int cls) {
+    const uint32_t mask = (1u << log2n) - 1;
+    uint32_t h = infra_hash(key, log2n);
+    for (uint32_t i = 0; i <= mask; ++i, h = (h + 1) & mask) {
+        const uint64_t e = tab[h];
+        if (e == 0) {
+            tab[h] = (key << 3) | (type << 2) | (uint64_t)cls;
+            return true;
+        }
+        if ((e >> 3) == key) return true;  // already present (same ideal)
+    }
+    return false;
+}
+
+// Returns the entry for key, or 0.
+__device__ __forceinline__ uint64_t infra_find(const uint64_t *tab, int log2n, uint64_t key) {
+    const uint32_t mask = (1u << log2n) - 1;
+    uint32_t h = infra_hash(key, log2n);
+    for (uint32_t i = 0; i <= mask; ++i, h = (h + 1) & mask) {
+        const uint64_t e = tab[h];
+        if (e == 0) return 0;
+        if ((e >> 3) == key) return e;
+    }
+    return 0;
+}
+
+}  // namespace eis

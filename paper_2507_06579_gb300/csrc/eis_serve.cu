@@ -174,7 +174,8 @@ bool launch_batch(eis_server *s, Slot &sl) {
         k_compact<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_sqfree, sl.d_tile_off, sl.d_surv);
         k_walk_persistent<<<s->grid, 256, 0, st>>>(sl.d_segs, nseg, sl.d_surv, sl.d_ctr,
                                                    sl.d_ctr + 1, sl.d_flags, nullptr, sl.d_steps,
-                                                   sl.d_status, s->step_limit);
+                                                   sl.d_status, s->step_limit, 0u, nullptr,
+                                                   nullptr, 0u);
         k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts);
     }
     cudaMemcpyAsync(sl.h_counts, sl.d_counts, 2 * nseg * sizeof(unsigned long long),

@@ -1,0 +1,220 @@
+// k_giant.cu -- infrastructure baby-step giant-step kernel (Algorithm 1),
+// one warp per discriminant, generator classes in Z/3 (Appendix A).
+//
+// Baby steps: lane 0 walks states j = 1..N from O_K (fp32 walk of
+// eis_common.cuh), stopping early at the centre of a short period.  Each
+// state goes into the warp's shared-memory table twice:
+//   direct  (Q_j, P_j)      -> S_j, the position delta_j of state j;
+//   mirror  (Q_j, P_{j+1})  -> S_j, which is state l - j (the period is
+//                               palindromic), position R - delta_j,
+// and O_K itself as (2, P_1) -> 0.  The table therefore covers the window
+// [R - delta_N, R + delta_N] around the regulator R.
+// Giant steps: G = state N+1; lane t starts at G^(t+2) and strides by G^32,
+// so round r looks up positions about (32 r + t + 2) delta_{N+1}.  Every
+// giant step is reduce(G^32 * mu) (eis_infra.cuh).  The stride is shorter than
+// the window, so the first hit in (round, lane) order is the first giant step
+// inside it:
+//   mirror hit on j (position R - delta_j, no wrap): log eps = g(mu) + S_j,
+//     because S_l - S_{l-j} = S_j;
+//   direct hit on j (position R + delta_j, one wrap): log eps = g(mu) - S_j.
+// G^2 already lies beyond delta_N, so no giant step can hit before the window.
+#include "eis_common.cuh"
+#include "eis_infra.cuh"
+#include "eis_kernels.h"
+
+namespace eis {
+
+namespace {
+
+struct GiantOut {
+    int g;         // log eps in Z/3, or -1 (error), or -2 (not in D)
+    uint32_t baby;
+    uint32_t giant;
+};
+
+// The BSGS of one d by one warp (all 32 lanes call it with the same d).
+__device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, uint32_t max_rounds) {
+    const int lane = threadIdx.x & 31;
+    GiantOut res{-1, 0, 0};
+    for (uint32_t i = lane; i < (1u << log2n); i += 32) tab[i] = 0;
+    __syncwarp();
+    // ---- baby steps (lane 0)
+    int done = 0, gres = 0, nb = 0;
+    int64_t Ga = 0, Gb = 0;
+    int Gg = 0;
+    if (lane == 0) {
+        WalkState w;
+        int g;
+        nb = 1;
+        if (walk_init(d, w, g)) {
+            done = 1;
+            gres = g;
+        } else {
+            const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
+            bool ok = infra_insert(tab, log2n, infra_key(2, P1), 0, 0);
+            for (int j = 1; j <= nbaby && ok; ++j) {
+                const int64_t Pj = __float_as_int(w.Pm) & 0x7fffff;
+                const int64_t Qj = (int64_t)w.Q;
+                const int Sj = (w.acc2 >> 1) % 3;
+                ok &= infra_insert(tab, log2n, infra_key(Qj, Pj), 0, Sj);
+                const bool centre = walk_step(w);
+                ++nb;
+                if (centre) {
+                    done = 1;
+                    gres = walk_finish(w);
+                    break;
+                }
+                const int64_t Pn = __float_as_int(w.Pm) & 0x7fffff;
+                ok &= infra_insert(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
+            }
+            if (!ok) {
+                done = 1;
+                gres = -1;
+            } else if (!done) {
+                Ga = (int64_t)w.Q / 2;
+                Gb = __float_as_int(w.Pm) & 0x7fffff;
+                Gg = (w.acc2 >> 1) % 3;
+            }
+        }
+    }
+    __syncwarp();
+    done = __shfl_sync(kFull, done, 0);
+    gres = __shfl_sync(kFull, gres, 0);
+    nb = __shfl_sync(kFull, nb, 0);
+    res.baby = (uint32_t)nb;
+    if (done) {
+        res.g = gres;
+        return res;
+    }
+    Ideal G;
+    G.a = __shfl_sync(kFull, Ga, 0);
+    G.b = __shfl_sync(kFull, Gb, 0);
+    G.g = __shfl_sync(kFull, Gg, 0);
+    const int64_t s = (int64_t)isqrt_u64(d);
+    const int64_t dd = (int64_t)d;
+    // ---- powers: P[i] = G^(2^i), i = 0..5 (the same on every lane)
+    Ideal pw[6];
+    pw[0] = G;
+    bool ok = true;
+    for (int i = 1; i < 6; ++i) ok &= ideal_mul(pw[i - 1], pw[i - 1], dd, s, pw[i]);
+    // lane t: mu = G^(t+2) by the bits of t+2 (2..33)
+    Ideal mu;
+    bool have = false;
+    const int k = lane + 2;
+    for (int i = 0; i < 6; ++i) {
+        if ((k >> i) & 1) {
+            if (!have) {
+                mu = pw[i];
+                have = true;
+            } else {
+                Ideal t;
+                ok &= ideal_mul(mu, pw[i], dd, s, t);
+                mu = t;
+            }
+        }
+    }
+    const Ideal stride = pw[5];  // G^32
+    uint32_t giants = 15;        // compositions spent on the powers (upper bound)
+    if (!__all_sync(kFull, ok)) return res;
+    for (uint32_t r = 0; r < max_rounds; ++r) {
+        const uint64_t e = infra_find(tab, log2n, infra_key(2 * mu.a, mu.b));
+        const unsigned hit = __ballot_sync(kFull, e != 0);
+        if (hit) {
+            const int win = __ffs(hit) - 1;
+            int g = 0;
+            if (lane == win) {
+                const int Sj = (int)(e & 3);
+                g = (e & 4) ? (mu.g + Sj) % 3 : (mu.g + 3 - Sj) % 3;
+            }
+            res.g = __shfl_sync(kFull, g, win);
+            res.giant = giants + 32 * r + (uint32_t)win;
+            return res;
+        }
+        Ideal t;
+        ok = ideal_mul(mu, stride, dd, s, t);
+        mu = t;
+        if (!__all_sync(kFull, ok)) return res;
+        giants += 32;
+    }
+    return res;  // no hit within max_rounds: error
+}
+
+__device__ __forceinline__ bool warp_squarefree(uint64_t d, const uint32_t *__restrict__ primes,
+                                                uint32_t nprimes) {
+    bool hit = false;
+    for (uint32_t i = threadIdx.x & 31; i < nprimes; i += 32) {
+        const uint64_t p = primes[i];
+        if (p * p > d) break;
+        if (d % (p * p) == 0) hit = true;
+    }
+    return !__any_sync(kFull, hit);
+}
+
+}  // namespace
+
+// One warp per item; items are taken from a global counter.
+//   ds != nullptr : item i is d = ds[i]; out_g[i] = 0 (not in D),
+//                   1 + log eps_d, or -1 (error); the square-free test runs
+//                   against the prime table.
+//   ds == nullptr : item i is candidate cands[i] of the Seg layout (already
+//                   square-free); its flag bit / log byte are written.
+// Dynamic shared memory: (blockDim.x / 32) tables of 2^log2n uint64.
+__global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
+                                               const Seg *__restrict__ segs, uint32_t nseg,
+                                               const uint32_t *__restrict__ cands,
+                                               const uint32_t *__restrict__ n_ptr, uint32_t n_fixed,
+                                               uint32_t *__restrict__ next_ptr,
+                                               const uint32_t *__restrict__ primes, uint32_t nprimes,
+                                               int8_t *__restrict__ out_g,
+                                               uint32_t *__restrict__ flags,
+                                               uint8_t *__restrict__ glog,
+                                               unsigned long long *__restrict__ acc,
+                                               int *__restrict__ status, int nbaby, int log2n,
+                                               uint32_t max_rounds) {
+    extern __shared__ uint64_t smem_tab[];
+    uint64_t *tab = smem_tab + (size_t)(threadIdx.x >> 5) * (1u << log2n);
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = n_ptr ? min(*n_ptr, n_fixed) : n_fixed;
+    unsigned long long baby = 0, giant = 0;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(next_ptr, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n) break;
+        if (ds) {
+            const uint64_t d = ds[item];
+            if (d % 8 != 5 || !warp_squarefree(d, primes, nprimes)) {
+                if (lane == 0) out_g[item] = 0;
+                continue;
+            }
+            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds);
+            if (lane == 0) {
+                out_g[item] = (int8_t)(r.g >= 0 ? 1 + r.g : -1);
+                if (r.g < 0) atomicOr(status, kErrGiant);
+            }
+            baby += r.baby;
+            giant += r.giant;
+        } else {
+            const uint32_t cand = cands[item];
+            const uint64_t d = cand_to_d(segs, nseg, cand);
+            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds);
+            if (lane == 0) {
+                if (r.g < 0) {
+                    atomicOr(status, kErrGiant);
+                } else {
+                    if (r.g == 0) atomicOr(&flags[cand >> 5], 1u << (cand & 31));
+                    if (glog) glog[cand] = (uint8_t)(1 + r.g);
+                }
+            }
+            baby += r.baby;
+            giant += r.giant;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && acc) {
+        atomicAdd(&acc[0], baby);
+        atomicAdd(&acc[1], giant);
+    }
+}
+
+}  // namespace eis

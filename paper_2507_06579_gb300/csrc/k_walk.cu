@@ -77,10 +77,15 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
     const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
     const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
     uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
-    unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit) {
+    unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
+    uint32_t defer_after, uint32_t *__restrict__ defer_list, uint32_t *__restrict__ defer_count,
+    uint32_t defer_cap) {
     const uint32_t n_surv = *n_surv_ptr;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    // A walk longer than defer_after steps is handed to the giant-step kernel
+    // (while the defer list has room); 0 disables deferral.
+    bool may_defer = defer_after != 0;
     WalkState w;
     walk_park_idle(w);
     bool active = false;
@@ -111,6 +116,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
                     } else {
                         active = true;
                         done = 0;
+                        may_defer = defer_after != 0;
                     }
                 }
             }
@@ -118,7 +124,8 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
         if (!__any_sync(kFull, active)) break;
         // Walk until some lane reaches its centre (or the step limit).  Idle
         // lanes hold NaN states whose centre test is false.
-        uint32_t room = active ? step_limit - done : 0xffffffffu;
+        const uint32_t cap = (active && may_defer) ? min(defer_after, step_limit) : step_limit;
+        uint32_t room = active ? cap - min(done, cap) : 0xffffffffu;
         for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
         uint32_t n = 0;
         bool hit;
@@ -137,6 +144,16 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
                 my_steps += done;
                 active = false;
                 walk_park_idle(w);
+            } else if (may_defer && done >= defer_after && done < step_limit) {
+                const uint32_t slot = atomicAdd(defer_count, 1u);
+                if (slot < defer_cap) {
+                    defer_list[slot] = cand;
+                    my_steps += done;
+                    active = false;
+                    walk_park_idle(w);
+                } else {
+                    may_defer = false;  // list full: this walk goes on here
+                }
             } else if (done >= step_limit) {
                 atomicOr(status, kErrSteps);
                 my_steps += done;
