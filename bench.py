@@ -310,7 +310,7 @@ def main():
         from paper_2507_06579_gb300 import workloads as W
         rates = []
         with E.Server(ctx) as srv:
-            for rate in (10.0, 100.0, 1000.0, 10000.0):
+            for rate in (10.0, 100.0, 1000.0, 3000.0, 10000.0):
                 n = int(min(max(rate * args.serve_seconds, 20), 30000))
                 reqs = W.serving_stream(n, rate, seed=5)
                 out = srv.replay([r[0] for r in reqs],
@@ -329,9 +329,35 @@ def main():
                                "[1e6, 1e12], L log-uniform in [1e2, 1e6]; 10% membership "
                                "queries on d == 5 mod 8 below 1e12 (not-square-free d answer "
                                "EIS_ENOTD); seed 5",
-                   "server": "4 slots x 2^22 candidates, continuous batching",
+                   "server": "4 slots x 2^22 candidates, continuous batching; walks past "
+                             "131072 baby steps and membership queries go to the warp-per-d "
+                             "giant-step kernel",
                    "rates": rates, "batches": sst["batches"],
                    "max_batch_parts": sst["max_batch_parts"]}
+
+    # single membership queries near 1e12 through eis_is_eisenstein: the
+    # warp-per-d giant-step kernel against the single-lane walk
+    membership = None
+    if args.serve_seconds > 0 and rank == 0:
+        rng = np.random.default_rng(6)
+        ds = [int(x) * 8 + 5 for x in rng.integers(10**12 // 8 - 10**9, 10**12 // 8, size=400)]
+        membership = {"workload": "400 random d == 5 mod 8 in [1e12 - 8e9, 1e12] (not-square-free "
+                                  "d included: they return EIS_ENOTD)"}
+        for name, mode in (("giant", E.EIS_MODE_PERSISTENT), ("plain", E.EIS_MODE_PLAIN)):
+            ctx.set_option(E.EIS_OPT_MODE, mode)
+            lat = []
+            for d in ds:
+                t1 = time.perf_counter()
+                try:
+                    ctx.is_eisenstein(d)
+                except E.EisError:
+                    pass
+                lat.append((time.perf_counter() - t1) * 1e3)
+            lat = np.array(lat)
+            membership[name] = {"p50_ms": float(np.percentile(lat, 50)),
+                                "p99_ms": float(np.percentile(lat, 99)),
+                                "max_ms": float(lat.max())}
+        ctx.set_option(E.EIS_OPT_MODE, E.EIS_MODE_PERSISTENT)
 
     # end to end through the public call with host buffers
     n_cand, _ = E.num_candidates(lo, hi)
@@ -385,6 +411,7 @@ def main():
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
                 "batched": batched,
                 "serving": serving,
+                "membership": membership,
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": launches, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)

@@ -251,6 +251,10 @@ typedef struct {
                               /* requests are split into parts                   */
     uint32_t slot_requests;   /* request parts one batch holds (4096)            */
     uint32_t max_pending;     /* queued parts before submit refuses (2^20)       */
+    uint32_t giant_after;     /* baby steps after which a walk is handed to the  */
+                              /* warp-per-d giant-step kernel (131072); this  */
+                              /* cuts the latency of batches holding a very   */
+                              /* long period; 0xffffffff: never               */
 } eis_server_config;
 
 typedef struct {

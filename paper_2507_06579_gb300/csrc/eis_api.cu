@@ -478,8 +478,14 @@ eis_ctx_view eis_ctx_get_view(eis_ctx *c) {
     v.nprimes = c->nprimes;
     const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : c->occ_persistent;
     v.walk_grid = (uint32_t)(c->sm_count * std::max(1, per_sm));
+    v.giant_grid = (uint32_t)(c->sm_count * 4);
     v.step_limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
     return v;
+}
+
+void eis_giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n) {
+    giant_params(d, forced, nbaby, log2n);
+    log2n = std::min(log2n, kGiantMaxLog2);
 }
 
 bool eis_ctx_reserve(eis_ctx *c, uint64_t bytes) {

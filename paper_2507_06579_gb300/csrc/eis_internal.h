@@ -11,8 +11,13 @@ struct eis_ctx_view {
     const uint32_t *d_primes;  // odd primes < 2^22 on the device
     uint32_t nprimes;
     uint32_t walk_grid;        // persistent walk grid (SMs x resident CTAs)
+    uint32_t giant_grid;       // one-warp blocks of k_giant that fit at once (SMs x 4)
     uint32_t step_limit;
 };
+
+// Baby-step count and log2 table size of the giant-step search for d up to
+// `d` (forced > 0 picks the baby-step count).
+void eis_giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n);
 
 eis_ctx_view eis_ctx_get_view(eis_ctx *ctx);
 // Account `bytes` of device memory against the context budget; false if over.

@@ -39,6 +39,7 @@ struct Part {
     uint64_t lo, hi;  // half-open, at most slot_candidates candidates
     uint64_t ncand;
     uint64_t d0;
+    bool member;      // a single d answered by the giant-step kernel
 };
 
 struct Request {
@@ -66,7 +67,13 @@ struct Slot {
     Tile *h_tiles = nullptr;
     unsigned long long *h_counts = nullptr;
     int *h_status = nullptr;
-    std::vector<Part> items;
+    // membership queries of the batch (one warp each in k_giant)
+    uint64_t *d_mem_d = nullptr, *h_mem_d = nullptr;
+    int8_t *d_mem_out = nullptr, *h_mem_out = nullptr;
+    unsigned char *d_mem_ctl = nullptr;  // [0] next, [8] acc[2], [24] status
+    uint32_t *d_defer = nullptr;         // long walks handed to k_giant
+    std::vector<Part> items;     // range segments
+    std::vector<Part> members;   // membership queries
     bool busy = false;
 };
 
@@ -78,7 +85,12 @@ struct eis_server {
     std::vector<Slot> slots;
     uint32_t max_tiles = 0;
     uint32_t grid = 0;
+    uint32_t giant_grid = 0;
     uint32_t step_limit = 1u << 26;
+    // walks longer than this many baby steps go to the giant-step kernel, which
+    // finishes one long walk far sooner than a single lane (0: never)
+    uint32_t defer_after = 131072;  // from eis_server_config.giant_after
+    uint32_t defer_cap = 0;
     std::mutex mu;
     std::condition_variable cv_work;  // dispatcher: new parts or stop
     std::condition_variable cv_done;  // waiters: a request finished
@@ -115,7 +127,13 @@ int slot_alloc(eis_server *s, Slot &sl) {
               cudaHostAlloc(&sl.h_segs, S * sizeof(Seg), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&sl.h_tiles, s->max_tiles * sizeof(Tile), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&sl.h_counts, (2 * S + 1) * sizeof(unsigned long long), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc(&sl.h_status, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
+              cudaHostAlloc(&sl.h_status, sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
+              cudaMalloc(&sl.d_mem_d, S * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&sl.d_mem_out, S) == cudaSuccess &&
+              cudaMalloc(&sl.d_mem_ctl, 64) == cudaSuccess &&
+              cudaMalloc(&sl.d_defer, (size_t)s->defer_cap * 4 + 4) == cudaSuccess &&
+              cudaHostAlloc(&sl.h_mem_d, S * sizeof(uint64_t), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&sl.h_mem_out, S, cudaHostAllocDefault) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return EIS_ENOMEM;
@@ -126,20 +144,22 @@ int slot_alloc(eis_server *s, Slot &sl) {
 void slot_free(Slot &sl) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     void *dev[] = {sl.d_segs, sl.d_tiles, sl.d_sqfree, sl.d_flags, sl.d_tile_pop, sl.d_tile_off,
-                   sl.d_surv, sl.d_ctr, sl.d_status, sl.d_counts, sl.d_steps};
+                   sl.d_surv, sl.d_ctr, sl.d_status, sl.d_counts, sl.d_steps,
+                   sl.d_mem_d, sl.d_mem_out, sl.d_mem_ctl, sl.d_defer};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *host[] = {sl.h_segs, sl.h_tiles, sl.h_counts, sl.h_status};
+    void *host[] = {sl.h_segs, sl.h_tiles, sl.h_counts, sl.h_status, sl.h_mem_d, sl.h_mem_out};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     if (sl.done_ev) cudaEventDestroy(sl.done_ev);
     if (sl.stream) cudaStreamDestroy(sl.stream);
 }
 
-uint64_t slot_bytes(const eis_server_config &c, uint32_t max_tiles) {
+uint64_t slot_bytes(const eis_server_config &c, uint32_t max_tiles, uint32_t defer_cap) {
     const uint64_t words = c.slot_candidates / 32 + c.slot_requests + 1;
-    return words * 4 * 2 + words * 32 * 4 + (uint64_t)max_tiles * (sizeof(Tile) + 8) +
-           (uint64_t)c.slot_requests * (sizeof(Seg) + 16) + 256;
+    return words * 4 * 2 + words * 32 * 4 + (uint64_t)defer_cap * 4 +
+           (uint64_t)max_tiles * (sizeof(Tile) + 8) +
+           (uint64_t)c.slot_requests * (sizeof(Seg) + 16 + 9) + 320;
 }
 
 // Launch one batch (the slot's items) on the slot's stream.
@@ -174,9 +194,37 @@ bool launch_batch(eis_server *s, Slot &sl) {
         k_compact<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_sqfree, sl.d_tile_off, sl.d_surv);
         k_walk_persistent<<<s->grid, 256, 0, st>>>(sl.d_segs, nseg, sl.d_surv, sl.d_ctr,
                                                    sl.d_ctr + 1, sl.d_flags, nullptr, sl.d_steps,
-                                                   sl.d_status, s->step_limit, 0u, nullptr,
-                                                   nullptr, 0u);
+                                                   sl.d_status, s->step_limit, s->defer_after,
+                                                   sl.d_defer, sl.d_ctr + 2, s->defer_cap);
+        if (s->defer_after) {
+            uint64_t dmax = 0;
+            for (const Part &p : sl.items) dmax = std::max(dmax, p.d0 + 8 * (p.ncand - 1));
+            int nbaby, log2n;
+            eis_giant_params(dmax, 0, nbaby, log2n);
+            k_giant<<<s->giant_grid, 32, (size_t)8 << log2n, st>>>(
+                nullptr, sl.d_segs, nseg, sl.d_defer, sl.d_ctr + 2, s->defer_cap, sl.d_ctr + 3,
+                cv.d_primes, cv.nprimes, nullptr, sl.d_flags, nullptr, sl.d_steps + 1,
+                sl.d_status, nbaby, log2n, 1u << 20);
+        }
         k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts);
+    }
+    const uint32_t nmem = (uint32_t)sl.members.size();
+    if (nmem > 0) {
+        uint64_t dmax = 0;
+        for (uint32_t i = 0; i < nmem; ++i) {
+            sl.h_mem_d[i] = sl.members[i].d0;
+            dmax = std::max(dmax, sl.members[i].d0);
+        }
+        int nbaby, log2n;
+        eis_giant_params(dmax, 0, nbaby, log2n);
+        cudaMemcpyAsync(sl.d_mem_d, sl.h_mem_d, nmem * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(sl.d_mem_ctl, 0, 64, st);
+        k_giant<<<std::min<uint32_t>(nmem, s->giant_grid), 32, (size_t)8 << log2n, st>>>(
+            sl.d_mem_d, nullptr, 0, nullptr, nullptr, nmem,
+            reinterpret_cast<uint32_t *>(sl.d_mem_ctl), cv.d_primes, cv.nprimes, sl.d_mem_out,
+            nullptr, nullptr, reinterpret_cast<unsigned long long *>(sl.d_mem_ctl + 8),
+            reinterpret_cast<int *>(sl.d_mem_ctl + 24), nbaby, log2n, 1u << 20);
+        cudaMemcpyAsync(sl.h_mem_out, sl.d_mem_out, nmem, cudaMemcpyDeviceToHost, st);
     }
     cudaMemcpyAsync(sl.h_counts, sl.d_counts, 2 * nseg * sizeof(unsigned long long),
                     cudaMemcpyDeviceToHost, st);
@@ -204,7 +252,7 @@ void dispatcher(eis_server *s) {
             if (q == cudaErrorNotReady) continue;
             std::lock_guard<std::mutex> lk(s->mu);
             const int bstatus = (q != cudaSuccess) ? EIS_EDEVICE
-                                : ((*sl.h_status & kErrSteps) ? EIS_ESTEPS : EIS_OK);
+                                : ((*sl.h_status & (kErrSteps | kErrGiant)) ? EIS_ESTEPS : EIS_OK);
             if (q != cudaSuccess) s->failed = true;
             for (size_t i = 0; i < sl.items.size(); ++i) {
                 auto it = s->reqs.find(sl.items[i].req);
@@ -215,7 +263,23 @@ void dispatcher(eis_server *s) {
                 if (bstatus != EIS_OK && r.status == EIS_OK) r.status = bstatus;
                 if (--r.parts_left == 0) finish_request(s, it->first, r);
             }
+            for (size_t i = 0; i < sl.members.size(); ++i) {
+                auto it = s->reqs.find(sl.members[i].req);
+                if (it == s->reqs.end()) continue;
+                Request &r = it->second;
+                const int8_t o = sl.h_mem_out[i];
+                if (q != cudaSuccess) {
+                    if (r.status == EIS_OK) r.status = EIS_EDEVICE;
+                } else if (o < 0) {
+                    if (r.status == EIS_OK) r.status = EIS_ESTEPS;
+                } else if (o > 0) {
+                    r.sumD += 1;
+                    r.sumE += (o == 1);
+                }
+                if (--r.parts_left == 0) finish_request(s, it->first, r);
+            }
             sl.items.clear();
+            sl.members.clear();
             sl.busy = false;
             progressed = true;
             s->cv_done.notify_all();
@@ -228,8 +292,19 @@ void dispatcher(eis_server *s) {
                 if (s->pending.empty() || s->failed) break;
                 uint64_t cand = 0;
                 uint32_t tiles = 0;
-                while (!s->pending.empty() && sl.items.size() < s->cfg.slot_requests) {
+                while (!s->pending.empty() && sl.items.size() < s->cfg.slot_requests &&
+                       sl.members.size() < s->cfg.slot_requests) {
                     const Part &p = s->pending.front();
+                    if (p.member) {
+                        auto itm = s->reqs.find(p.req);
+                        if (itm != s->reqs.end() && itm->second.cancelled) {
+                            if (--itm->second.parts_left == 0) finish_request(s, itm->first, itm->second);
+                        } else {
+                            sl.members.push_back(p);
+                        }
+                        s->pending.pop_front();
+                        continue;
+                    }
                     const uint64_t c = (p.ncand + 31) / 32 * 32;
                     const uint32_t t = (uint32_t)((p.ncand + kTileCands - 1) / kTileCands);
                     if (!sl.items.empty() &&
@@ -248,10 +323,11 @@ void dispatcher(eis_server *s) {
                     sl.items.push_back(p);
                     s->pending.pop_front();
                 }
-                if (sl.items.empty()) continue;
+                if (sl.items.empty() && sl.members.empty()) continue;
                 s->st.batches++;
-                s->st.parts += sl.items.size();
-                s->st.max_batch_parts = std::max<uint64_t>(s->st.max_batch_parts, sl.items.size());
+                s->st.parts += sl.items.size() + sl.members.size();
+                s->st.max_batch_parts = std::max<uint64_t>(s->st.max_batch_parts,
+                                                           sl.items.size() + sl.members.size());
             }
             if (!launch_batch(s, sl)) {
                 std::lock_guard<std::mutex> lk(s->mu);
@@ -304,7 +380,9 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
         if (cfg->slot_candidates) c.slot_candidates = cfg->slot_candidates;
         if (cfg->slot_requests) c.slot_requests = cfg->slot_requests;
         if (cfg->max_pending) c.max_pending = cfg->max_pending;
+        c.giant_after = cfg->giant_after;
     }
+    if (c.giant_after == 0) c.giant_after = 131072;
     if (c.slots > 64 || c.slot_candidates < 64 || c.slot_candidates > ((uint64_t)1 << 30) ||
         c.slot_requests < 1)
         return EIS_EINVAL;
@@ -316,8 +394,11 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
     s->cfg = c;
     s->max_tiles = (uint32_t)(c.slot_candidates / kTileCands) + c.slot_requests + 1;
     s->grid = v.walk_grid;
+    s->defer_after = c.giant_after == 0xffffffffu ? 0u : c.giant_after;
+    s->giant_grid = v.giant_grid;
     s->step_limit = v.step_limit;
-    const uint64_t need = slot_bytes(c, s->max_tiles) * c.slots;
+    s->defer_cap = (uint32_t)std::max<uint64_t>(1024, c.slot_candidates / 8);
+    const uint64_t need = slot_bytes(c, s->max_tiles, s->defer_cap) * c.slots;
     if (!eis_ctx_reserve(ctx, need)) {
         delete s;
         return EIS_ENOMEM;
@@ -351,7 +432,7 @@ int eis_server_submit(eis_server *s, int kind, uint64_t lo, uint64_t hi, uint64_
     for (uint64_t off = 0; off < n; off += M) {
         const uint64_t a = d0 + 8 * off;
         const uint64_t b = std::min(hi, d0 + 8 * (off + M));
-        parts.push_back(Part{0, a, b, std::min<uint64_t>(M, n - off), a});
+        parts.push_back(Part{0, a, b, std::min<uint64_t>(M, n - off), a, kind == EIS_REQ_MEMBER});
     }
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return EIS_EINVAL;

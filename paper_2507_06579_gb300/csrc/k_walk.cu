@@ -73,7 +73,10 @@ __global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t c
 // K5.  The survivor queue surv[0, *n_surv) holds global candidate indices in
 // increasing order; lanes take them from the end (largest d first within the
 // Seg layout, which is sorted by d0) so that the cheapest walks run last.
-__global__ void __launch_bounds__(256) k_walk_persistent(
+// kDefer: walks longer than defer_after steps are handed to the giant-step
+// kernel; the kernel without it carries none of that bookkeeping.
+template <bool kDefer>
+__device__ __forceinline__ void walk_persistent_body(
     const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
     const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
     uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
@@ -84,8 +87,8 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     // A walk longer than defer_after steps is handed to the giant-step kernel
-    // (while the defer list has room); 0 disables deferral.
-    bool may_defer = defer_after != 0;
+    // (while the defer list has room).
+    bool may_defer = kDefer;
     WalkState w;
     walk_park_idle(w);
     bool active = false;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
                     } else {
                         active = true;
                         done = 0;
-                        may_defer = defer_after != 0;
+                        may_defer = kDefer;
                     }
                 }
             }
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
         if (!__any_sync(kFull, active)) break;
         // Walk until some lane reaches its centre (or the step limit).  Idle
         // lanes hold NaN states whose centre test is false.
-        const uint32_t cap = (active && may_defer) ? min(defer_after, step_limit) : step_limit;
+        const uint32_t cap = (kDefer && active && may_defer) ? min(defer_after, step_limit) : step_limit;
         uint32_t room = active ? cap - min(done, cap) : 0xffffffffu;
         for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
         uint32_t n = 0;
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
                 my_steps += done;
                 active = false;
                 walk_park_idle(w);
-            } else if (may_defer && done >= defer_after && done < step_limit) {
+            } else if (kDefer && may_defer && done >= defer_after && done < step_limit) {
                 const uint32_t slot = atomicAdd(defer_count, 1u);
                 if (slot < defer_cap) {
                     defer_list[slot] = cand;
@@ -163,6 +166,22 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
         }
     }
     add_steps(steps_acc, my_steps);
+}
+
+__global__ void __launch_bounds__(256) k_walk_persistent(
+    const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
+    const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
+    uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
+    unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
+    uint32_t defer_after, uint32_t *__restrict__ defer_list, uint32_t *__restrict__ defer_count,
+    uint32_t defer_cap) {
+    if (defer_after == 0)
+        walk_persistent_body<false>(segs, nseg, surv, n_surv_ptr, next_ptr, flags, glog, steps_acc,
+                                    status, step_limit, 0, nullptr, nullptr, 0);
+    else
+        walk_persistent_body<true>(segs, nseg, surv, n_surv_ptr, next_ptr, flags, glog, steps_acc,
+                                   status, step_limit, defer_after, defer_list, defer_count,
+                                   defer_cap);
 }
 
 // Membership query for one d (one warp).  out[0] = 0 (d not in D) or
