@@ -219,6 +219,10 @@ int eis_plan_launch(eis_plan *plan, void *stream);
 /* Wait for the last launch and copy the per-interval #E to counts_out[n]. */
 int eis_plan_counts(eis_plan *plan, uint64_t *counts_out);
 
+/* Wait for the last launch and copy the per-interval #D (square-free
+ * candidates, Section 1) to counts_D_out[n]. */
+int eis_plan_counts_D(eis_plan *plan, uint64_t *counts_D_out);
+
 /* Device pointers to the plan's bitmaps (valid until eis_plan_destroy):
  * flags/sqfree words for the concatenated candidates; interval i starts at
  * word word_offset[i] (host array of n entries, written if non-NULL). */

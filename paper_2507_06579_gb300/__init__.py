@@ -126,6 +126,7 @@ SIGNATURES = [
     ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
     ("eis_plan_launch", _I32, [_VP, _VP]),
     ("eis_plan_counts", _I32, [_VP, _VP]),
+    ("eis_plan_counts_D", _I32, [_VP, _VP]),
     ("eis_plan_bitmaps", _I32, [_VP, _P(_VP), _P(_VP), _VP, _P(_U64)]),
     ("eis_plan_copy_bitmaps", _I32, [_VP, _VP, _VP, _I32]),
     ("eis_plan_stats", _I32, [_VP, _P(Stats)]),
@@ -202,6 +203,12 @@ class Plan:
     def counts(self):
         out = np.zeros(max(self.n, 1), dtype=np.uint64)
         _check(lib().eis_plan_counts(self.handle, out.ctypes.data), "eis_plan_counts")
+        return out[: self.n]
+
+    def counts_D(self):
+        """Per-interval #D (square-free candidates) of the last launch."""
+        out = np.zeros(max(self.n, 1), dtype=np.uint64)
+        _check(lib().eis_plan_counts_D(self.handle, out.ctypes.data), "eis_plan_counts_D")
         return out[: self.n]
 
     def stats(self) -> dict:

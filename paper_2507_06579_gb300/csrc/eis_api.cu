@@ -654,6 +654,17 @@ int eis_plan_counts(eis_plan *p, uint64_t *counts_out) {
     return plan_counts_user(p, counts_out);
 }
 
+int eis_plan_counts_D(eis_plan *p, uint64_t *counts_D_out) {
+    if (!p || (!counts_D_out && p->n)) return EIS_EINVAL;
+    int rc = plan_wait(p);
+    if (rc != EIS_OK) return rc;
+    std::vector<unsigned long long> cnt(2 * p->segs.size() + 1);
+    EIS_CK(cudaMemcpy(cnt.data(), p->d_counts, cnt.size() * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < p->segs.size(); ++i) counts_D_out[p->user_of[i]] = cnt[2 * i + 1];
+    return EIS_OK;
+}
+
 int eis_plan_bitmaps(eis_plan *p, const uint32_t **flags, const uint32_t **sqfree,
                      uint64_t *word_offset, uint64_t *total_words) {
     if (!p) return EIS_EINVAL;
