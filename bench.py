@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip tuning the walk settings on a sample below the window")
     ap.add_argument("--batched-steps", type=int, default=2,
                     help="passes of the 4096-interval batched workload (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
@@ -215,6 +217,11 @@ def main():
     E.build()
     ctx = E.Context(local)
     lo, hi = rank_window(rank, int(args.window))
+    tuned = None
+    if not args.no_autotune:
+        # tune on a 1e8-wide sample just below the window (outside the timed region)
+        tlo = max(5, lo - 10**8)
+        tuned = ctx.autotune(tlo, lo)
     plan = ctx.plan_create([lo], [hi], E.EIS_MODE_PERSISTENT)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -406,6 +413,7 @@ def main():
                            "discriminants_per_step": nD, "candidates_per_step": sts[0]["candidates"],
                            "baby_steps_per_step": steps_per_launch, "pi_E_window": count,
                            "l2": "flushed between steps (512 MiB write)",
+                           "autotuned": tuned,
                            "parallelism": "dp%d (independent windows)" % world},
                 "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,

@@ -165,6 +165,28 @@ int eis_count_batch(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t
                     uint64_t *counts_out);
 
 /* ---------------------------------------------------------------------
+ * Autotuning
+ * ------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t ctas_per_sm;     /* persistent walk CTAs per SM chosen */
+    int64_t giant_threshold; /* baby steps before a walk goes to the giant-step */
+                             /* kernel (0: never), i.e. 1 or 32 threads per d   */
+    int64_t giant_stride;    /* giant-step baby count N (0: automatic)         */
+    double ms_best;          /* device time of one pass with the chosen setting */
+    double ms_default;       /* ... and with the context's previous setting     */
+    int32_t trials;          /* settings timed                                  */
+} eis_tune_result;
+
+/* Time candidate settings (CTAs per SM of the persistent walk, deferral of
+ * long walks to the warp-per-d giant-step kernel and its threshold, the
+ * giant-step baby count) on the sample [lo, hi) -- a window of the d-range
+ * the context will serve -- and keep the fastest in the context.  Every
+ * candidate runs a full plan (sieve, walks, count); results are identical
+ * for every setting, only time differs.  Takes a few passes of the sample. */
+int eis_autotune(eis_ctx *ctx, uint64_t lo, uint64_t hi, eis_tune_result *out);
+
+/* ---------------------------------------------------------------------
  * Classification without device allocation
  * ------------------------------------------------------------------- */
 

@@ -90,6 +90,15 @@ def build(force: bool = False) -> str:
     return _build.build(force=force)
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("giant_threshold", ctypes.c_int64),
+                ("giant_stride", ctypes.c_int64), ("ms_best", ctypes.c_double),
+                ("ms_default", ctypes.c_double), ("trials", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("slot_candidates", ctypes.c_uint64),
                 ("slot_requests", ctypes.c_uint32), ("max_pending", ctypes.c_uint32),
@@ -122,6 +131,7 @@ SIGNATURES = [
     ("eis_classify_range_log", _I32, [_VP, _U64, _U64, _VP, _I32, _VP]),
     ("eis_is_eisenstein", _I32, [_VP, _U64, _P(_I32)]),
     ("eis_count_batch", _I32, [_VP, _VP, _VP, _SZ, _VP]),
+    ("eis_autotune", _I32, [_VP, _U64, _U64, _P(TuneResult)]),
     ("eis_classify_range_noalloc", _I32, [_I32, _U64, _U64, _VP, _VP, _P(_U64), _VP]),
     ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
     ("eis_plan_launch", _I32, [_VP, _VP]),
@@ -432,6 +442,35 @@ class Context:
         _check(lib().eis_count_batch(self.handle, lo.ctypes.data, hi.ctypes.data, len(lo),
                                      out.ctypes.data), "eis_count_batch")
         return out[: len(lo)]
+
+    def autotune(self, lo: int, hi: int, cache_path: str | None = None) -> dict:
+        """Pick the persistent-walk and giant-step settings for the d-range of
+        the sample [lo, hi) (eis_autotune) and keep them in this context.
+        With cache_path, results are stored per decade of hi in a JSON file
+        and reused instead of re-timing."""
+        import json
+        import math
+        key = "decade_%d" % int(math.log10(max(hi, 10)))
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        if key in cache:
+            r = cache[key]
+            self.set_option(EIS_OPT_CTAS_PER_SM, r["ctas_per_sm"])
+            self.set_option(EIS_OPT_GIANT_THRESHOLD, r["giant_threshold"])
+            self.set_option(EIS_OPT_GIANT_STRIDE, r["giant_stride"])
+            return dict(r, cached=True)
+        res = TuneResult()
+        _check(lib().eis_autotune(self.handle, lo, hi, ctypes.byref(res)), "eis_autotune")
+        r = res.as_dict()
+        if cache_path:
+            cache[key] = r
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, cache_path)
+        return dict(r, cached=False)
 
     def plan_create(self, los, his, mode: int = EIS_MODE_PERSISTENT) -> Plan:
         return Plan(self, los, his, mode)

@@ -700,6 +700,83 @@ int eis_plan_destroy(eis_plan *p) {
     return EIS_OK;
 }
 
+int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
+    if (!c || !out || lo >= hi) return EIS_EINVAL;
+    if (hi > EIS_D_LIMIT) return EIS_ERANGE;
+    struct Setting {
+        int ctas;
+        int64_t thr, stride;
+    };
+    const int occ = c->occ_persistent;
+    std::vector<Setting> cands;
+    for (int ctas : {occ, std::max(1, occ * 3 / 4), std::max(1, occ / 2)})
+        for (int64_t thr : {(int64_t)0, (int64_t)131072, (int64_t)32768})
+            for (int64_t stride : {(int64_t)0, (int64_t)2048})
+                if (thr != 0 || stride == 0) cands.push_back({ctas, thr, stride});
+    const Setting prev{c->ctas_per_sm, c->giant_threshold, c->giant_stride};
+    const int prev_mode = c->mode;
+    c->mode = EIS_MODE_PERSISTENT;
+    auto time_one = [&](const Setting &st, double &ms, uint64_t &count) -> int {
+        c->ctas_per_sm = st.ctas;
+        c->giant_threshold = st.thr;
+        c->giant_stride = st.stride;
+        eis_plan *p = nullptr;
+        int rc = plan_build(c, &lo, &hi, 1, EIS_MODE_PERSISTENT, 0, &p);
+        if (rc != EIS_OK) return rc;
+        double best = 1e300;
+        for (int rep = 0; rep < 2 && rc == EIS_OK; ++rep) {
+            rc = plan_launch(p, c->stream);
+            eis_stats stt{};
+            if (rc == EIS_OK) rc = plan_fill_stats(p, &stt);
+            if (rc == EIS_OK) {
+                best = std::min(best, stt.ms_total);
+                count = stt.in_E;
+            }
+        }
+        plan_free(p);
+        ms = best;
+        return rc;
+    };
+    double ms_prev = 0;
+    uint64_t ref_count = 0, cnt = 0;
+    int rc = time_one(prev, ms_prev, ref_count);
+    Setting best = prev;
+    double ms_best = ms_prev;
+    int trials = 1;
+    for (const Setting &st : cands) {
+        if (rc != EIS_OK) break;
+        double ms = 0;
+        rc = time_one(st, ms, cnt);
+        if (rc != EIS_OK) break;
+        if (cnt != ref_count) {  // every setting must give the same count
+            rc = EIS_EDEVICE;
+            break;
+        }
+        ++trials;
+        if (ms < ms_best) {
+            ms_best = ms;
+            best = st;
+        }
+    }
+    c->mode = prev_mode;
+    if (rc != EIS_OK) {
+        c->ctas_per_sm = prev.ctas;
+        c->giant_threshold = prev.thr;
+        c->giant_stride = prev.stride;
+        return rc;
+    }
+    c->ctas_per_sm = best.ctas;
+    c->giant_threshold = best.thr;
+    c->giant_stride = best.stride;
+    out->ctas_per_sm = best.ctas > 0 ? best.ctas : occ;
+    out->giant_threshold = best.thr;
+    out->giant_stride = best.stride;
+    out->ms_best = ms_best;
+    out->ms_default = ms_prev;
+    out->trials = trials;
+    return EIS_OK;
+}
+
 int eis_count_range(eis_ctx *c, uint64_t lo, uint64_t hi, uint64_t *count_out) {
     if (!c || !count_out) return EIS_EINVAL;
     eis_stats acc{};
