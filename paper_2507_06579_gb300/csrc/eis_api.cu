@@ -77,6 +77,7 @@ struct eis_plan {
     uint8_t *d_glog = nullptr;
     uint32_t *d_defer = nullptr;  // candidates handed to the giant-step kernel
     uint32_t defer_cap = 0, defer_after = 0;
+    int fast = 1;                 // every d of the plan is below kFastDLimit
     int giant_nbaby = 0, giant_log2n = 0;
     uint32_t giant_grid = 0;
     uint64_t bytes = 0;
@@ -184,7 +185,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
             k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
                 p->d_segs, nseg, p->d_surv, p->d_ctr, p->d_ctr + 1, p->d_flags, p->d_glog,
                 p->d_steps, p->d_status, limit, p->defer_after, p->d_defer, p->d_ctr + 2,
-                p->defer_cap);
+                p->defer_cap, p->fast);
             ++launches;
             record(p->ev[2], s, capturing);
             if (p->d_defer) {
@@ -266,6 +267,8 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     }
     p->total_cand = cur;
     p->nwords = cur / 32;
+    for (const Seg &sg : p->segs)
+        if (sg.ncand && sg.d0 + 8 * (sg.ncand - 1) >= kFastDLimit) p->fast = 0;
     // Survivor indices are 32-bit and the queue head may overshoot by one
     // claim per warp.
     if (cur > 0xffffffffull - (1ull << 24)) {

@@ -24,6 +24,14 @@
 //   * P is carried as P + 2^23, so the float's low mantissa bits are P itself
 //     and P mod 4 is one AND on the bit pattern.
 //
+// Fast quotient (d < kFastDLimit): the walk carries num' = P + s + 1/2, so
+// num'/Q = q + (r + 1/2)/Q lies at least 1/(2Q) from every integer.  With
+// |rcp(Q) - 1/Q| <= 2^-23 / Q the product num' * rcp(Q) errs by less than
+// num' 2^-23 / Q < 1/(2Q) while num' < 2^22, so one FMA rounded toward -inf
+// onto 2^23 gives 2^23 + q exactly and no correction is needed.  The
+// remainder comes out as r + 1/2, and P' + 2^23 = (s + 2^23) - (r + 1/2)
+// rounded up (the exact value is the half-integer P' + 2^23 - 1/2).
+//
 // Half period: the P's and Q's of one period are palindromic,
 // Q_j = Q_{l-j} and P_j = P_{l+1-j}; the walk stops at the centre, which is
 // the first j with Q_{j+1} = Q_j (l = 2j+1) or P_{j+1} = P_j (l = 2j), the
@@ -55,6 +63,10 @@ struct Tile {
     uint32_t seg;    // index into the Seg table
     uint32_t ncand;  // candidates in this tile
 };
+
+// d below this use the fast quotient: 2 sqrt(d) + 1/2 < 2^22 for every
+// d <= (2^21 - 1)^2 = 4398042316801.
+constexpr uint64_t kFastDLimit = 4390000000000ull;
 
 // Error codes written by kernels into the plan's status word.
 constexpr int kErrSteps = 1;  // a baby walk ran past its step limit
@@ -99,6 +111,7 @@ __device__ __forceinline__ void walk_park_idle(WalkState &w) {
 // First step from (P_0, Q_0) = (1, 2) in 64-bit integers: q_0 = floor((1+s)/2),
 // P_1 = 2 q_0 - 1, Q_1 = (d - P_1^2)/2.  Returns true when the period is 1
 // (Q_1 = Q_0 = 2), with *g = log eps_d; otherwise leaves the state at j = 1.
+template <bool kFast>
 __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
     const uint64_t s = isqrt_u64(d);
     const uint64_t a0 = (1 + s) >> 1;
@@ -112,8 +125,10 @@ __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
     w.Pm = __fadd_rn(__uint2float_rn((uint32_t)P1), kMagic);
     w.Q = __uint2float_rn((uint32_t)Q1);
     w.Qp = 2.0f;
-    w.soff = __fsub_rn(__uint2float_rn((uint32_t)s), kMagic);
-    w.sm = __fadd_rn(__uint2float_rn((uint32_t)s), kMagic);
+    const float sf = __uint2float_rn((uint32_t)s);
+    w.soff = kFast ? __fsub_rn(__fadd_rn(sf, 0.5f), kMagic)   // s + 1/2 - 2^23
+                   : __fsub_rn(sf, kMagic);                    // s - 2^23
+    w.sm = __fadd_rn(sf, kMagic);
     w.acc2 = 2 * c1;
     return false;
 }
@@ -121,17 +136,28 @@ __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
 // One baby step j -> j+1.  Always advances the state and adds
 // 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2; returns true when the
 // new state is the centre of the period (Q_{j+1} = Q_j or P_{j+1} = P_j).
+template <bool kFast>
 __device__ __forceinline__ bool walk_step(WalkState &w) {
-    const float num = __fadd_rn(w.Pm, w.soff);                // P_j + s
-    const float rq = rcp_approx(w.Q);
-    const float qm = __fmaf_rd(num, rq, kMagic - 0.5f);       // 2^23 + (q or q-1)
-    float qf = __fsub_rn(qm, kMagic);
-    float r = __fmaf_rn(-qf, w.Q, num);                       // remainder, in [0, 2Q)
-    if (r >= w.Q) {
-        r = __fsub_rn(r, w.Q);
-        qf = __fadd_rn(qf, 1.0f);                             // q_j
+    float qf, Pn;
+    if (kFast) {
+        const float num = __fadd_rn(w.Pm, w.soff);            // P_j + s + 1/2
+        const float rq = rcp_approx(w.Q);
+        const float qm = __fmaf_rd(num, rq, kMagic);          // 2^23 + q exactly
+        qf = __fsub_rn(qm, kMagic);
+        const float r = __fmaf_rn(-qf, w.Q, num);             // r + 1/2
+        Pn = __fsub_ru(w.sm, r);                              // P_{j+1} + 2^23
+    } else {
+        const float num = __fadd_rn(w.Pm, w.soff);            // P_j + s
+        const float rq = rcp_approx(w.Q);
+        const float qm = __fmaf_rd(num, rq, kMagic - 0.5f);   // 2^23 + (q or q-1)
+        qf = __fsub_rn(qm, kMagic);
+        float r = __fmaf_rn(-qf, w.Q, num);                   // remainder, in [0, 2Q)
+        if (r >= w.Q) {
+            r = __fsub_rn(r, w.Q);
+            qf = __fadd_rn(qf, 1.0f);                         // q_j
+        }
+        Pn = __fsub_rn(w.sm, r);                              // P_{j+1} + 2^23 = s - r + 2^23
     }
-    const float Pn = __fsub_rn(w.sm, r);                      // P_{j+1} + 2^23 = s - r + 2^23
     const float dP = __fsub_rn(w.Pm, Pn);                     // P_j - P_{j+1}
     const float Qn = __fmaf_rn(qf, dP, w.Qp);                 // Q_{j+1}
     w.acc2 += 2 + (__float_as_int(Pn) & 2);

@@ -27,7 +27,7 @@ __global__ void k_walk_persistent(const Seg *segs, uint32_t nseg, const uint32_t
                                   const uint32_t *n_surv_ptr, uint32_t *next_ptr, uint32_t *flags,
                                   uint8_t *glog, unsigned long long *steps_acc, int *status,
                                   uint32_t step_limit, uint32_t defer_after, uint32_t *defer_list,
-                                  uint32_t *defer_count, uint32_t defer_cap);
+                                  uint32_t *defer_count, uint32_t defer_cap, int fast);
 __global__ void k_giant(const uint64_t *ds, const Seg *segs, uint32_t nseg, const uint32_t *cands,
                         const uint32_t *n_ptr, uint32_t n_fixed, uint32_t *next_ptr,
                         const uint32_t *primes, uint32_t nprimes, int8_t *out_g, uint32_t *flags,

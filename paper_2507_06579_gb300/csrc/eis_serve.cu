@@ -187,6 +187,8 @@ bool launch_batch(eis_server *s, Slot &sl) {
     cudaMemsetAsync(sl.d_status, 0, sizeof(int), st);
     cudaMemsetAsync(sl.d_counts, 0, (2 * nseg + 1) * sizeof(unsigned long long), st);
     cudaMemsetAsync(sl.d_steps, 0, 4 * sizeof(unsigned long long), st);
+    uint64_t dmax = 0;
+    for (const Part &p : sl.items) dmax = std::max(dmax, p.d0 + 8 * (p.ncand - 1));
     if (nt > 0) {
         k_sieve<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_segs, cv.d_primes, cv.nprimes, sl.d_sqfree,
                                     sl.d_tile_pop);
@@ -195,10 +197,9 @@ bool launch_batch(eis_server *s, Slot &sl) {
         k_walk_persistent<<<s->grid, 256, 0, st>>>(sl.d_segs, nseg, sl.d_surv, sl.d_ctr,
                                                    sl.d_ctr + 1, sl.d_flags, nullptr, sl.d_steps,
                                                    sl.d_status, s->step_limit, s->defer_after,
-                                                   sl.d_defer, sl.d_ctr + 2, s->defer_cap);
+                                                   sl.d_defer, sl.d_ctr + 2, s->defer_cap,
+                                                   dmax < kFastDLimit ? 1 : 0);
         if (s->defer_after) {
-            uint64_t dmax = 0;
-            for (const Part &p : sl.items) dmax = std::max(dmax, p.d0 + 8 * (p.ncand - 1));
             int nbaby, log2n;
             eis_giant_params(dmax, 0, nbaby, log2n);
             k_giant<<<s->giant_grid, 32, (size_t)8 << log2n, st>>>(

@@ -32,6 +32,48 @@ struct GiantOut {
     uint32_t giant;
 };
 
+// Lane 0's baby phase: states 1..N into the table (direct and mirror keys);
+// done = 1 with gres = log eps_d if the centre comes first (or gres = -1 if
+// the table overflowed); otherwise G = state N+1.
+template <bool kFast>
+__device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n, int nbaby,
+                                           int &done, int &gres, int &nb, int64_t &Ga,
+                                           int64_t &Gb, int &Gg) {
+    WalkState w;
+    int g;
+    nb = 1;
+    if (walk_init<kFast>(d, w, g)) {
+        done = 1;
+        gres = g;
+        return;
+    }
+    const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
+    bool ok = infra_insert(tab, log2n, infra_key(2, P1), 0, 0);
+    for (int j = 1; j <= nbaby && ok; ++j) {
+        const int64_t Pj = __float_as_int(w.Pm) & 0x7fffff;
+        const int64_t Qj = (int64_t)w.Q;
+        const int Sj = (w.acc2 >> 1) % 3;
+        ok &= infra_insert(tab, log2n, infra_key(Qj, Pj), 0, Sj);
+        const bool centre = walk_step<kFast>(w);
+        ++nb;
+        if (centre) {
+            done = 1;
+            gres = walk_finish(w);
+            return;
+        }
+        const int64_t Pn = __float_as_int(w.Pm) & 0x7fffff;
+        ok &= infra_insert(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
+    }
+    if (!ok) {
+        done = 1;
+        gres = -1;
+        return;
+    }
+    Ga = (int64_t)w.Q / 2;
+    Gb = __float_as_int(w.Pm) & 0x7fffff;
+    Gg = (w.acc2 >> 1) % 3;
+}
+
 // The BSGS of one d by one warp (all 32 lanes call it with the same d).
 __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, uint32_t max_rounds) {
     const int lane = threadIdx.x & 31;
@@ -43,39 +85,10 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
     int64_t Ga = 0, Gb = 0;
     int Gg = 0;
     if (lane == 0) {
-        WalkState w;
-        int g;
-        nb = 1;
-        if (walk_init(d, w, g)) {
-            done = 1;
-            gres = g;
-        } else {
-            const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
-            bool ok = infra_insert(tab, log2n, infra_key(2, P1), 0, 0);
-            for (int j = 1; j <= nbaby && ok; ++j) {
-                const int64_t Pj = __float_as_int(w.Pm) & 0x7fffff;
-                const int64_t Qj = (int64_t)w.Q;
-                const int Sj = (w.acc2 >> 1) % 3;
-                ok &= infra_insert(tab, log2n, infra_key(Qj, Pj), 0, Sj);
-                const bool centre = walk_step(w);
-                ++nb;
-                if (centre) {
-                    done = 1;
-                    gres = walk_finish(w);
-                    break;
-                }
-                const int64_t Pn = __float_as_int(w.Pm) & 0x7fffff;
-                ok &= infra_insert(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
-            }
-            if (!ok) {
-                done = 1;
-                gres = -1;
-            } else if (!done) {
-                Ga = (int64_t)w.Q / 2;
-                Gb = __float_as_int(w.Pm) & 0x7fffff;
-                Gg = (w.acc2 >> 1) % 3;
-            }
-        }
+        if (d < kFastDLimit)
+            baby_phase<true>(d, tab, log2n, nbaby, done, gres, nb, Ga, Gb, Gg);
+        else
+            baby_phase<false>(d, tab, log2n, nbaby, done, gres, nb, Ga, Gb, Gg);
     }
     __syncwarp();
     done = __shfl_sync(kFull, done, 0);

@@ -228,7 +228,8 @@ extern "C" int eis_classify_range_noalloc(int device, uint64_t lo, uint64_t hi, 
     k_walk_persistent<<<g_na_grid[device], 256, 0, s>>>(
         reinterpret_cast<const Seg *>(base + kOffSeg), 1u,
         reinterpret_cast<const uint32_t *>(base + kOffQueue), ctr, ctr + 1, flags_out, nullptr,
-        c64, reinterpret_cast<int *>(ctr + 2), 1u << 26, 0u, nullptr, nullptr, 0u);
+        c64, reinterpret_cast<int *>(ctr + 2), 1u << 26, 0u, nullptr, nullptr, 0u,
+        d0 + 8 * (n - 1) < kFastDLimit ? 1 : 0);
     k_na_count<<<(nwords + 255) / 256 < 304 ? (nwords + 255) / 256 : 304, 256, 0, s>>>(nwords, flags_out, sq);
     if (cudaGetLastError() != cudaSuccess) return EIS_EDEVICE;
     unsigned long long host[4] = {0, 0, 0, 0};

@@ -25,6 +25,23 @@ __device__ __forceinline__ void add_steps(unsigned long long *acc, unsigned long
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
 }
 
+// One whole half-period walk by one thread: false past step_limit steps;
+// otherwise g = log eps_d and n = steps after the first.
+template <bool kFast>
+__device__ __forceinline__ bool walk_one(uint64_t d, uint32_t step_limit, int &g, uint32_t &n) {
+    WalkState w;
+    n = 0;
+    if (walk_init<kFast>(d, w, g)) return true;
+    for (;;) {
+        if (walk_step<kFast>(w)) { n += 1; break; }
+        if (walk_step<kFast>(w)) { n += 2; break; }
+        n += 2;
+        if (n >= step_limit) return false;
+    }
+    g = walk_finish(w);
+    return true;
+}
+
 // K2.  Candidates [cand_first, cand_first + ncand) of one Seg, d of the first
 // one = d_first.  cand_first is a multiple of 32, so each warp owns whole
 // flag words and writes them without atomics.
@@ -42,25 +59,15 @@ __global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t c
     unsigned long long steps = 0;
     if (valid && ((sqfree[cand >> 5] >> (cand & 31)) & 1u)) {
         const uint64_t d = d_first + 8ull * i;
-        WalkState w;
         int g;
+        uint32_t n = 0;
         steps = 1;
-        if (!walk_init(d, w, g)) {
-            uint32_t n = 0;
-            bool hit = false;
-            for (;;) {
-                if (walk_step(w)) { n += 1; hit = true; break; }
-                if (walk_step(w)) { n += 2; hit = true; break; }
-                n += 2;
-                if (n >= step_limit) break;
-            }
-            steps += n;
-            if (hit) {
-                g = walk_finish(w);
-            } else {
-                atomicOr(status, kErrSteps);
-                g = -1;
-            }
+        const bool ok = (d < kFastDLimit) ? walk_one<true>(d, step_limit, g, n)
+                                          : walk_one<false>(d, step_limit, g, n);
+        steps += n;
+        if (!ok) {
+            atomicOr(status, kErrSteps);
+            g = -1;
         }
         inE = (g == 0);
         if (glog && g >= 0) glog[cand] = (uint8_t)(1 + g);
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t c
 // Seg layout, which is sorted by d0) so that the cheapest walks run last.
 // kDefer: walks longer than defer_after steps are handed to the giant-step
 // kernel; the kernel without it carries none of that bookkeeping.
-template <bool kDefer>
+template <bool kDefer, bool kFast>
 __device__ __forceinline__ void walk_persistent_body(
     const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
     const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
@@ -113,7 +120,7 @@ __device__ __forceinline__ void walk_persistent_body(
                     const uint64_t d = cand_to_d(segs, nseg, cand);
                     int g;
                     my_steps += 1;
-                    if (walk_init(d, w, g)) {
+                    if (walk_init<kFast>(d, w, g)) {
                         record_result(flags, glog, cand, g);
                         walk_park_idle(w);
                     } else {
@@ -133,9 +140,9 @@ __device__ __forceinline__ void walk_persistent_body(
         uint32_t n = 0;
         bool hit;
         for (;;) {
-            hit = walk_step(w);
+            hit = walk_step<kFast>(w);
             if (__any_sync(kFull, hit)) { n += 1; break; }
-            hit = walk_step(w);
+            hit = walk_step<kFast>(w);
             if (__any_sync(kFull, hit)) { n += 2; break; }
             n += 2;
             if (n >= room) break;
@@ -174,14 +181,17 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
     uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
     uint32_t defer_after, uint32_t *__restrict__ defer_list, uint32_t *__restrict__ defer_count,
-    uint32_t defer_cap) {
-    if (defer_after == 0)
-        walk_persistent_body<false>(segs, nseg, surv, n_surv_ptr, next_ptr, flags, glog, steps_acc,
-                                    status, step_limit, 0, nullptr, nullptr, 0);
-    else
-        walk_persistent_body<true>(segs, nseg, surv, n_surv_ptr, next_ptr, flags, glog, steps_acc,
-                                   status, step_limit, defer_after, defer_list, defer_count,
-                                   defer_cap);
+    uint32_t defer_cap, int fast) {
+#define EIS_WALK_BODY(D, F)                                                                     \
+    walk_persistent_body<D, F>(segs, nseg, surv, n_surv_ptr, next_ptr, flags, glog, steps_acc, \
+                               status, step_limit, defer_after, defer_list, defer_count,        \
+                               defer_cap)
+    if (defer_after == 0) {
+        if (fast) EIS_WALK_BODY(false, true); else EIS_WALK_BODY(false, false);
+    } else {
+        if (fast) EIS_WALK_BODY(true, true); else EIS_WALK_BODY(true, false);
+    }
+#undef EIS_WALK_BODY
 }
 
 // Membership query for one d (one warp).  out[0] = 0 (d not in D) or
@@ -203,22 +213,13 @@ __global__ void __launch_bounds__(32) k_walk_single(uint64_t d, const uint32_t *
         out[1] = 0;
         return;
     }
-    WalkState w;
     int g;
-    uint32_t n = 1;
-    if (!walk_init(d, w, g)) {
-        uint32_t k = 0;
-        bool hit = false;
-        for (;;) {
-            if (walk_step(w)) { k += 1; hit = true; break; }
-            if (walk_step(w)) { k += 2; hit = true; break; }
-            k += 2;
-            if (k >= step_limit) break;
-        }
-        n += k;
-        if (hit) {
-            g = walk_finish(w);
-        } else {
+    uint32_t k = 0;
+    const bool ok = (d < kFastDLimit) ? walk_one<true>(d, step_limit, g, k)
+                                      : walk_one<false>(d, step_limit, g, k);
+    const uint32_t n = 1 + k;
+    {
+        if (!ok) {
             atomicOr(status, kErrSteps);
             g = -1;
         }

@@ -101,6 +101,8 @@ def test_small_config_log_matches_theta(ctx, orc):
     (10**6, 10**6 + 8 * (2 * 65536 + 37)),         # three tiles, ragged tail
     (10**9 + 3, 10**9 + 8 * 65536 + 11),           # exactly one tile + 1
     (E.EIS_D_LIMIT - 2000, E.EIS_D_LIMIT),         # top of the supported range
+    (4389999990000, 4390000000000),                # fast quotient just below its limit
+    (4390000000000 - 800, 4390000000000 + 800),    # a plan straddling that limit
 ])
 def test_edge_ranges(ctx, orc, in_mode, lo, hi):
     ref = orc.classify_range(lo, hi)["codes"]
