@@ -428,6 +428,7 @@ def main():
     plan.destroy()
     ctx.close()
     if dist is not None:
+        dist.barrier()  # rank 0 ran the extra legs; meet before tearing down
         dist.destroy_process_group()
     return 0
 

@@ -114,3 +114,15 @@ def test_rank_failure_then_resume(orc, tmp_path):
     first = {tuple(b) for c in res[1]["calls"] for b in c}
     assert not (redone & first)  # rank 1 did not recount its journaled blocks
     assert res2[0]["calls"] == []  # rank 0 had finished everything before the timeout
+
+
+def test_bench_rank_windows_are_disjoint():
+    import bench
+    ws = [bench.rank_window(r, 10**9) for r in range(8)]
+    for (lo, hi) in ws:
+        assert hi - lo == 10**9 + 1 and hi <= 10**11 + 1
+    for (a, b), (c, d) in zip(ws, ws[1:]):
+        assert d <= a + 1  # rank r+1's window lies below rank r's
+    # windows overlap only in their shared endpoint, which is == 0 mod 8 (no candidate)
+    for (a, b), (c, d) in zip(ws, ws[1:]):
+        assert d - 1 == a and a % 8 == 0
