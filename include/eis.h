@@ -234,6 +234,26 @@ int eis_classify_range_noalloc(int device, uint64_t lo, uint64_t hi, uint32_t *f
 int eis_plan_create(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t n,
                     int mode, eis_plan **out);
 
+/* Plan flags (eis_plan_create_ex). */
+#define EIS_PLAN_CLASSES 1u /* keep log eps_d per candidate and count the class  */
+                            /* of eps_d in F_4* per interval                     */
+#define EIS_PLAN_PRIMES 2u  /* classify the prime d == 5 (mod 8) only: the      */
+                            /* "square-free" bitmap and #D then hold the primes, */
+                            /* #E counts E cap P (Section 3.2)                   */
+
+/* eis_plan_create with flags (EIS_PLAN_*). */
+int eis_plan_create_ex(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
+                       uint32_t flags, eis_plan **out);
+
+/* For a plan made with EIS_PLAN_CLASSES: out[3 i + g] = number of d in
+ * interval i with eps_d == omega^g (mod 2O_K), g = 0 (d in E), 1, 2. */
+int eis_plan_class_counts(eis_plan *plan, uint64_t *out);
+
+/* Class counts over [lo, hi): out[g] = #{d in D : eps_d == omega^g mod 2O_K}
+ * (primes_only: over the prime d only).  The a-priori expectation is 1/3 each
+ * (Section 1). */
+int eis_class_counts(eis_ctx *ctx, uint64_t lo, uint64_t hi, int primes_only, uint64_t out[3]);
+
 /* Enqueue one full pass (sieve, walk, count) on `stream` (NULL: the
  * context's stream).  Asynchronous; allocates nothing. */
 int eis_plan_launch(eis_plan *plan, void *stream);

@@ -89,6 +89,12 @@ def lib():
             L.orc_count_range.argtypes = [u64, u64, i32, ctypes.POINTER(u64 * 3)]
             L.orc_sqfree_range.restype = i32
             L.orc_sqfree_range.argtypes = [u64, u64, i32, ctypes.c_void_p, ctypes.POINTER(u64)]
+            L.orc_is_prime.restype = i32
+            L.orc_is_prime.argtypes = [u64]
+            L.orc_classify_range_primes.restype = i32
+            L.orc_classify_range_primes.argtypes = [u64, u64, i32, ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_count_range_primes.restype = i32
+            L.orc_count_range_primes.argtypes = [u64, u64, i32, ctypes.POINTER(u64 * 3)]
             L.orc_num_candidates.restype = u64
             L.orc_num_candidates.argtypes = [u64, u64, ctypes.POINTER(u64)]
             L.orc_default_threads.restype = i32
@@ -103,6 +109,35 @@ def isqrt(n: int) -> int:
 
 def is_squarefree(n: int) -> bool:
     return bool(lib().orc_is_squarefree(n))
+
+
+def is_prime(n: int) -> bool:
+    return bool(lib().orc_is_prime(n))
+
+
+def classify_range_primes(lo: int, hi: int, nthreads: int = 0, thetas: bool = False):
+    """Per-candidate codes over the primes == 5 (mod 8) of [lo, hi): 0 (not
+    prime), 1 (prime not in E), 2 (prime in E); optionally theta codes."""
+    n, d0 = num_candidates(lo, hi)
+    codes = np.zeros(n, dtype=np.uint8)
+    th = np.zeros(n, dtype=np.uint8) if thetas else None
+    rc = lib().orc_classify_range_primes(lo, hi, nthreads, codes.ctypes.data if n else None,
+                                         th.ctypes.data if (th is not None and n) else None)
+    if rc != ORC_OK:
+        raise RuntimeError("orc_classify_range_primes(%d, %d) failed with %d" % (lo, hi, rc))
+    out = {"d0": d0, "codes": codes}
+    if th is not None:
+        out["thetas"] = th
+    return out
+
+
+def count_range_primes(lo: int, hi: int, nthreads: int = 0):
+    """(#primes == 5 mod 8, #(E cap P), rho steps) over [lo, hi)."""
+    out = (ctypes.c_uint64 * 3)()
+    rc = lib().orc_count_range_primes(lo, hi, nthreads, ctypes.byref(out))
+    if rc != ORC_OK:
+        raise RuntimeError("orc_count_range_primes(%d, %d) failed with %d" % (lo, hi, rc))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def in_D(d: int) -> bool:

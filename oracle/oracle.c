@@ -62,6 +62,14 @@ int orc_is_squarefree(uint64_t n) {
     return 1;
 }
 
+int orc_is_prime(uint64_t n) {
+    /* Definition: n >= 2 with no divisor k, 2 <= k <= sqrt(n). */
+    if (n < 2) return 0;
+    for (uint64_t k = 2; k <= n / k; k++)
+        if (n % k == 0) return 0;
+    return 1;
+}
+
 int orc_in_D(uint64_t d) {
     /* Section 1: d > 0, d == 5 (mod 8), square-free. */
     return d > 0 && d % 8 == 5 && orc_is_squarefree(d);
@@ -536,6 +544,7 @@ typedef struct {
     uint64_t cnt[3];         /* #D, #E, steps (atomic adds) */
     int err;                 /* first error (atomic) */
     int sieve_only;          /* 1: codes = 1 for d in D, no walk */
+    int primes;              /* 1: only prime d (prime subsequence, Section 3.2) */
 } range_job;
 
 #define ORC_BLOCK 4096
@@ -560,10 +569,19 @@ static void *range_worker(void *arg) {
         uint64_t dlo = J->d0 + 8 * b, dhi = J->d0 + 8 * (e - 1); /* inclusive */
         memset(notsf, 0, (size_t)(e - b));
         for (uint64_t k = 2; k <= dhi / k; k++) {
-            uint64_t k2 = k * k;
-            uint64_t x = (dlo + k2 - 1) / k2 * k2; /* least multiple >= dlo */
-            for (; x <= dhi; x += k2) {
-                if (x % 8 == 5) notsf[(x - dlo) / 8] = 1;
+            if (J->primes) {
+                /* composite: a multiple k*j with j >= k (so k*j != k) */
+                uint64_t x = (dlo + k - 1) / k * k;
+                if (x < k * k) x = k * k;
+                for (; x <= dhi; x += k) {
+                    if (x % 8 == 5) notsf[(x - dlo) / 8] = 1;
+                }
+            } else {
+                uint64_t k2 = k * k;
+                uint64_t x = (dlo + k2 - 1) / k2 * k2; /* least multiple >= dlo */
+                for (; x <= dhi; x += k2) {
+                    if (x % 8 == 5) notsf[(x - dlo) / 8] = 1;
+                }
             }
         }
         for (uint64_t kk = b; kk < e; kk++) {
@@ -602,11 +620,12 @@ static void *range_worker(void *arg) {
 
 static int run_range(uint64_t lo, uint64_t hi, int nthreads, uint8_t *codes,
                      uint32_t *periods, uint8_t *thetas, uint64_t out[3],
-                     int sieve_only) {
+                     int sieve_only, int primes) {
     if (hi < lo) return ORC_EINVAL;
     range_job J;
     memset(&J, 0, sizeof(J));
     J.sieve_only = sieve_only;
+    J.primes = primes;
     J.n = orc_num_candidates(lo, hi, &J.d0);
     J.codes = codes;
     J.periods = periods;
@@ -629,17 +648,26 @@ static int run_range(uint64_t lo, uint64_t hi, int nthreads, uint8_t *codes,
 
 int orc_classify_range(uint64_t lo, uint64_t hi, int nthreads, uint8_t *codes,
                        uint32_t *periods, uint8_t *thetas) {
-    return run_range(lo, hi, nthreads, codes, periods, thetas, NULL, 0);
+    return run_range(lo, hi, nthreads, codes, periods, thetas, NULL, 0, 0);
+}
+
+int orc_classify_range_primes(uint64_t lo, uint64_t hi, int nthreads, uint8_t *codes,
+                              uint8_t *thetas) {
+    return run_range(lo, hi, nthreads, codes, NULL, thetas, NULL, 0, 1);
+}
+
+int orc_count_range_primes(uint64_t lo, uint64_t hi, int nthreads, uint64_t out[3]) {
+    return run_range(lo, hi, nthreads, NULL, NULL, NULL, out, 0, 1);
 }
 
 int orc_count_range(uint64_t lo, uint64_t hi, int nthreads, uint64_t out[3]) {
-    return run_range(lo, hi, nthreads, NULL, NULL, NULL, out, 0);
+    return run_range(lo, hi, nthreads, NULL, NULL, NULL, out, 0, 0);
 }
 
 int orc_sqfree_range(uint64_t lo, uint64_t hi, int nthreads, uint8_t *in_D_out,
                      uint64_t *count_out) {
     uint64_t cnt[3] = {0, 0, 0};
-    int rc = run_range(lo, hi, nthreads, in_D_out, NULL, NULL, cnt, 1);
+    int rc = run_range(lo, hi, nthreads, in_D_out, NULL, NULL, cnt, 1, 0);
     if (count_out) *count_out = cnt[0];
     return rc;
 }

@@ -39,6 +39,10 @@ uint64_t orc_isqrt(uint64_t n);
  * Definition of "square-free" in the set D, Section 1. */
 int orc_is_squarefree(uint64_t n);
 
+/* 1 iff n is prime (trial division by every k with k^2 <= n).  For the
+ * prime subsequence E cap P of Section 3.2. */
+int orc_is_prime(uint64_t n);
+
 /* 1 iff d is in D = { d > 0 : d == 5 (mod 8), d square-free }, Section 1. */
 int orc_in_D(uint64_t d);
 
@@ -102,6 +106,14 @@ int orc_count_range(uint64_t lo, uint64_t hi, int nthreads, uint64_t out[3]);
  * multiples of k^2 for every k >= 2 (the definition applied to a block). */
 int orc_sqfree_range(uint64_t lo, uint64_t hi, int nthreads, uint8_t *in_D_out,
                      uint64_t *count_out);
+
+/* The same for the prime candidates only (Section 3.2, E cap P): codes[k] =
+ * 0 (d not prime), 1 (prime, not in E), 2 (prime in E); primality by marking,
+ * for every k >= 2, the multiples k*j with j >= k. */
+int orc_classify_range_primes(uint64_t lo, uint64_t hi, int nthreads, uint8_t *codes,
+                              uint8_t *thetas);
+/* out[0] = #primes == 5 (mod 8), out[1] = #(E cap P), out[2] = rho steps. */
+int orc_count_range_primes(uint64_t lo, uint64_t hi, int nthreads, uint64_t out[3]);
 
 /* Number of candidates d == 5 (mod 8) in [lo, hi) and the first one. */
 uint64_t orc_num_candidates(uint64_t lo, uint64_t hi, uint64_t *d0_out);

@@ -52,6 +52,9 @@ EIS_D_LIMIT = 1 << 44
 EIS_MODE_PLAIN = 0
 EIS_MODE_PERSISTENT = 1
 
+EIS_PLAN_CLASSES = 1
+EIS_PLAN_PRIMES = 2
+
 EIS_OPT_MODE = 1
 EIS_OPT_CTAS_PER_SM = 2
 EIS_OPT_THREADS = 3
@@ -134,6 +137,9 @@ SIGNATURES = [
     ("eis_autotune", _I32, [_VP, _U64, _U64, _P(TuneResult)]),
     ("eis_classify_range_noalloc", _I32, [_I32, _U64, _U64, _VP, _VP, _P(_U64), _VP]),
     ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
+    ("eis_plan_create_ex", _I32, [_VP, _VP, _VP, _SZ, _I32, ctypes.c_uint32, _P(_VP)]),
+    ("eis_plan_class_counts", _I32, [_VP, _VP]),
+    ("eis_class_counts", _I32, [_VP, _U64, _U64, _I32, _VP]),
     ("eis_plan_launch", _I32, [_VP, _VP]),
     ("eis_plan_counts", _I32, [_VP, _VP]),
     ("eis_plan_counts_D", _I32, [_VP, _VP]),
@@ -197,15 +203,23 @@ def num_candidates(lo: int, hi: int):
 class Plan:
     """A device-resident pipeline over fixed intervals (eis_plan_*)."""
 
-    def __init__(self, ctx: "Context", los, his, mode: int):
+    def __init__(self, ctx: "Context", los, his, mode: int, flags: int = 0):
         self.ctx = ctx
         self.los = _u64_array(los)
         self.his = _u64_array(his)
         self.n = len(self.los)
+        self.flags = flags
         h = ctypes.c_void_p()
-        _check(lib().eis_plan_create(ctx.handle, self.los.ctypes.data, self.his.ctypes.data,
-                                     self.n, mode, ctypes.byref(h)), "eis_plan_create")
+        _check(lib().eis_plan_create_ex(ctx.handle, self.los.ctypes.data, self.his.ctypes.data,
+                                        self.n, mode, flags, ctypes.byref(h)), "eis_plan_create_ex")
         self.handle = h
+
+    def class_counts(self):
+        """(n, 3) array: per interval the number of d with eps_d == omega^g
+        mod 2O_K, g = 0, 1, 2 (needs EIS_PLAN_CLASSES)."""
+        out = np.zeros(3 * max(self.n, 1), dtype=np.uint64)
+        _check(lib().eis_plan_class_counts(self.handle, out.ctypes.data), "eis_plan_class_counts")
+        return out[: 3 * self.n].reshape(self.n, 3)
 
     def launch(self, stream=None):
         _check(lib().eis_plan_launch(self.handle, _stream_handle(stream)), "eis_plan_launch")
@@ -472,8 +486,15 @@ class Context:
             os.replace(tmp, cache_path)
         return dict(r, cached=False)
 
-    def plan_create(self, los, his, mode: int = EIS_MODE_PERSISTENT) -> Plan:
-        return Plan(self, los, his, mode)
+    def plan_create(self, los, his, mode: int = EIS_MODE_PERSISTENT, flags: int = 0) -> Plan:
+        return Plan(self, los, his, mode, flags)
+
+    def class_counts(self, lo: int, hi: int, primes_only: bool = False):
+        """[#{eps_d == 1}, #{eps_d == omega}, #{eps_d == omega^2}] over [lo, hi)."""
+        out = np.zeros(3, dtype=np.uint64)
+        _check(lib().eis_class_counts(self.handle, lo, hi, 1 if primes_only else 0,
+                                      out.ctypes.data), "eis_class_counts")
+        return [int(x) for x in out]
 
 
 def _is_device(t) -> bool:

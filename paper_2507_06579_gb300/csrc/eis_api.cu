@@ -75,6 +75,8 @@ struct eis_plan {
     unsigned long long *d_counts = nullptr;  // [2 s] #E, [2 s + 1] #D
     unsigned long long *d_steps = nullptr;   // [0] baby, [1] giant, [2] deferred
     uint8_t *d_glog = nullptr;
+    unsigned long long *d_cls = nullptr;  // [3 s + g] #{d : log eps_d = g} (EIS_PLAN_CLASSES)
+    int primes_only = 0;          // EIS_PLAN_PRIMES: classify prime d only
     uint32_t *d_defer = nullptr;  // candidates handed to the giant-step kernel
     uint32_t defer_cap = 0, defer_after = 0;
     int fast = 1;                 // every d of the plan is below kFastDLimit
@@ -173,9 +175,10 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
     EIS_CK(cudaMemsetAsync(p->d_counts, 0, 2 * nseg * sizeof(unsigned long long) + 8, s));
     EIS_CK(cudaMemsetAsync(p->d_steps, 0, 4 * sizeof(unsigned long long), s));
     if (p->d_glog) EIS_CK(cudaMemsetAsync(p->d_glog, 0, p->total_cand, s));
+    if (p->d_cls) EIS_CK(cudaMemsetAsync(p->d_cls, 0, 3 * nseg * sizeof(unsigned long long) + 8, s));
     if (ntiles > 0) {
         k_sieve<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_segs, c->d_primes, c->nprimes, p->d_sqfree,
-                                       p->d_tile_pop);
+                                       p->d_tile_pop, p->primes_only);
         ++launches;
         if (p->mode == EIS_MODE_PERSISTENT) {
             k_scan_tiles<<<1, 1024, 0, s>>>(p->d_tile_pop, p->d_tile_off, ntiles, p->d_ctr);
@@ -209,7 +212,8 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
             record(p->ev[2], s, capturing);
             record(p->ev[4], s, capturing);
         }
-        k_count<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_flags, p->d_sqfree, p->d_counts);
+        k_count<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_flags, p->d_sqfree, p->d_counts, p->d_glog,
+                                       p->d_cls);
         ++launches;
     } else {
         record(p->ev[1], s, capturing);
@@ -230,7 +234,7 @@ static void plan_free(eis_plan *p) {
         if (e) cudaEventDestroy(e);
     void *bufs[] = {p->d_segs, p->d_tiles, p->d_sqfree, p->d_flags, p->d_tile_pop, p->d_tile_off,
                     p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog,
-                    p->d_defer};
+                    p->d_defer, p->d_cls};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->ctx) p->ctx->in_use -= std::min(p->ctx->in_use, p->bytes);
@@ -238,7 +242,9 @@ static void plan_free(eis_plan *p) {
 }
 
 static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
-                      int with_log, eis_plan **out) {
+                      int with_log, eis_plan **out, uint32_t flags = 0) {
+    if (flags & ~(uint32_t)(EIS_PLAN_CLASSES | EIS_PLAN_PRIMES)) return EIS_EINVAL;
+    if (flags & EIS_PLAN_CLASSES) with_log = 1;
     if (!c || !out || (n && (!lo || !hi))) return EIS_EINVAL;
     if (mode != EIS_MODE_PLAIN && mode != EIS_MODE_PERSISTENT) return EIS_EINVAL;
     for (size_t i = 0; i < n; ++i) {
@@ -250,6 +256,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     p->ctx = c;
     p->mode = mode;
     p->n = n;
+    p->primes_only = (flags & EIS_PLAN_PRIMES) ? 1 : 0;
     std::vector<uint64_t> d0(n), nc(n);
     for (size_t i = 0; i < n; ++i) nc[i] = num_candidates(lo[i], hi[i], &d0[i]);
     std::vector<uint32_t> order(n);
@@ -309,6 +316,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     EIS_ALLOC(p->d_counts, 2 * nseg * sizeof(unsigned long long) + 8);
     EIS_ALLOC(p->d_steps, 4 * sizeof(unsigned long long));
     if (with_log) EIS_ALLOC(p->d_glog, p->total_cand);
+    if (flags & EIS_PLAN_CLASSES) EIS_ALLOC(p->d_cls, 3 * nseg * sizeof(unsigned long long) + 8);
     if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && p->total_cand > 0) {
         uint64_t dmax = 0;
         for (const Seg &sg : p->segs)
@@ -645,6 +653,53 @@ int eis_get_stats(eis_ctx *c, eis_stats *out) {
 int eis_plan_create(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
                     eis_plan **out) {
     return plan_build(c, lo, hi, n, mode, 0, out);
+}
+
+int eis_plan_create_ex(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
+                       uint32_t flags, eis_plan **out) {
+    return plan_build(c, lo, hi, n, mode, 0, out, flags);
+}
+
+int eis_plan_class_counts(eis_plan *p, uint64_t *out) {
+    if (!p || (!out && p->n)) return EIS_EINVAL;
+    if (!p->d_cls) return EIS_EINVAL;
+    int rc = plan_wait(p);
+    if (rc != EIS_OK) return rc;
+    std::vector<unsigned long long> cnt(3 * p->segs.size() + 1);
+    EIS_CK(cudaMemcpy(cnt.data(), p->d_cls, cnt.size() * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < p->segs.size(); ++i)
+        for (int g = 0; g < 3; ++g) out[3 * p->user_of[i] + g] = cnt[3 * i + g];
+    return EIS_OK;
+}
+
+int eis_class_counts(eis_ctx *c, uint64_t lo, uint64_t hi, int primes_only, uint64_t out[3]) {
+    if (!c || !out) return EIS_EINVAL;
+    if (lo > hi) return EIS_EINVAL;
+    if (hi > EIS_D_LIMIT) return EIS_ERANGE;
+    uint64_t d0;
+    const uint64_t ntot = num_candidates(lo, hi, &d0);
+    const uint64_t M = max_chunk_cands(c, 1);
+    if (M == 0) return EIS_ENOMEM;
+    uint64_t acc[3] = {0, 0, 0};
+    const uint32_t flags = EIS_PLAN_CLASSES | (primes_only ? EIS_PLAN_PRIMES : 0u);
+    for (uint64_t off = 0; off < ntot; off += M) {
+        const uint64_t a = lo + 8 * off;
+        const uint64_t b = std::min(hi, lo + 8 * (off + M));
+        eis_plan *p = nullptr;
+        int rc = plan_build(c, &a, &b, 1, c->mode == EIS_MODE_PLAIN ? EIS_MODE_PLAIN
+                                                                     : EIS_MODE_PERSISTENT,
+                            1, &p, flags);
+        if (rc != EIS_OK) return rc;
+        rc = plan_launch(p, c->stream);
+        uint64_t part[3] = {0, 0, 0};
+        if (rc == EIS_OK) rc = eis_plan_class_counts(p, part);
+        plan_free(p);
+        if (rc != EIS_OK) return rc;
+        for (int g = 0; g < 3; ++g) acc[g] += part[g];
+    }
+    for (int g = 0; g < 3; ++g) out[g] = acc[g];
+    return EIS_OK;
 }
 
 int eis_plan_launch(eis_plan *p, void *stream) {

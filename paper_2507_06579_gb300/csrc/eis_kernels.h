@@ -9,13 +9,13 @@
 namespace eis {
 
 __global__ void k_sieve(const Tile *tiles, const Seg *segs, const uint32_t *primes,
-                        uint32_t nprimes, uint32_t *sqfree, uint32_t *tile_pop);
+                        uint32_t nprimes, uint32_t *sqfree, uint32_t *tile_pop, int primes_only);
 __global__ void k_scan_tiles(const uint32_t *tile_pop, uint32_t *tile_off, uint32_t ntiles,
                              uint32_t *total);
 __global__ void k_compact(const Tile *tiles, const uint32_t *sqfree, const uint32_t *tile_off,
                           uint32_t *surv);
 __global__ void k_count(const Tile *tiles, const uint32_t *flags, const uint32_t *sqfree,
-                        unsigned long long *counts);
+                        unsigned long long *counts, const uint8_t *glog, unsigned long long *cls);
 __global__ void k_expand_codes(const uint32_t *flags, const uint32_t *sqfree, uint64_t ncand,
                                uint8_t *codes);
 __global__ void k_fill(uint32_t *buf, uint64_t nwords, uint32_t v);

@@ -191,7 +191,7 @@ bool launch_batch(eis_server *s, Slot &sl) {
     for (const Part &p : sl.items) dmax = std::max(dmax, p.d0 + 8 * (p.ncand - 1));
     if (nt > 0) {
         k_sieve<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_segs, cv.d_primes, cv.nprimes, sl.d_sqfree,
-                                    sl.d_tile_pop);
+                                    sl.d_tile_pop, 0);
         k_scan_tiles<<<1, 1024, 0, st>>>(sl.d_tile_pop, sl.d_tile_off, nt, sl.d_ctr);
         k_compact<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_sqfree, sl.d_tile_off, sl.d_surv);
         k_walk_persistent<<<s->grid, 256, 0, st>>>(sl.d_segs, nseg, sl.d_surv, sl.d_ctr,
@@ -207,7 +207,8 @@ bool launch_batch(eis_server *s, Slot &sl) {
                 cv.d_primes, cv.nprimes, nullptr, sl.d_flags, nullptr, sl.d_steps + 1,
                 sl.d_status, nbaby, log2n, 1u << 20);
         }
-        k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts);
+        k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts, nullptr,
+                                    nullptr);
     }
     const uint32_t nmem = (uint32_t)sl.members.size();
     if (nmem > 0) {

@@ -65,11 +65,15 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *red, u
 
 // K1: one CTA per tile.  sqfree bit k = [candidate k is square-free];
 // tile_pop[t] = number of square-free candidates of tile t.
+// primes_only: bit k = [candidate k is prime] instead (prime subsequence,
+// Section 3.2).  For an odd prime p, p m == 5 (mod 8) iff m == 5p (mod 8)
+// (p^2 == 1 mod 8), so the multiples p m (m >= 2) among the candidates are
+// p apart in candidate index.
 __global__ void __launch_bounds__(256) k_sieve(const Tile *__restrict__ tiles,
                                                const Seg *__restrict__ segs,
                                                const uint32_t *__restrict__ primes,
                                                uint32_t nprimes, uint32_t *__restrict__ sqfree,
-                                               uint32_t *__restrict__ tile_pop) {
+                                               uint32_t *__restrict__ tile_pop, int primes_only) {
     __shared__ uint32_t bits[kTileWords];
     __shared__ uint32_t red[32];
     const Tile t = tiles[blockIdx.x];
@@ -86,6 +90,32 @@ __global__ void __launch_bounds__(256) k_sieve(const Tile *__restrict__ tiles,
         bits[w] = v;
     }
     __syncthreads();
+    if (primes_only) {
+        uint32_t i = 0;
+        // small primes: the whole CTA strides over the hits of one prime
+        for (; i < nprimes; ++i) {
+            const uint64_t p = primes[i];
+            if (p >= 1024 || p * p > dlast) break;
+            uint64_t m = (dfirst + p - 1) / p;
+            if (m < 2) m = 2;
+            m += (5 * p + 8 - m % 8) % 8;  // m == 5p (mod 8)
+            const uint64_t dh = m * p;
+            if (dh > dlast) continue;
+            const uint32_t first = (uint32_t)((dh - dfirst) >> 3);
+            const uint32_t nh = (uint32_t)((dlast - dh) / (8 * p)) + 1;
+            for (uint32_t h = threadIdx.x; h < nh; h += blockDim.x)
+                clear_bit(bits, first + h * (uint32_t)p);
+        }
+        for (uint32_t j = i + threadIdx.x; j < nprimes; j += blockDim.x) {
+            const uint64_t p = primes[j];
+            if (p * p > dlast) break;
+            uint64_t m = (dfirst + p - 1) / p;
+            if (m < 2) m = 2;
+            m += (5 * p + 8 - m % 8) % 8;
+            for (uint64_t dh = m * p; dh <= dlast; dh += 8 * p)
+                clear_bit(bits, (uint32_t)((dh - dfirst) >> 3));
+        }
+    } else {
     // Small primes: the whole CTA strides over the hits of one prime.
     uint32_t i = 0;
     for (; i < nprimes; ++i) {
@@ -110,6 +140,7 @@ __global__ void __launch_bounds__(256) k_sieve(const Tile *__restrict__ tiles,
         m += (13 - m % 8) % 8;
         for (uint64_t dh = m * p2; dh <= dlast; dh += 8 * p2)
             clear_bit(bits, (uint32_t)((dh - dfirst) >> 3));
+    }
     }
     __syncthreads();
     uint32_t pop = 0;
@@ -177,10 +208,14 @@ __global__ void __launch_bounds__(256) k_compact(const Tile *__restrict__ tiles,
 
 // K4: per-interval counts.  counts[2*seg] += #E, counts[2*seg+1] += #D over
 // the tile's words (ballot/popcount data already packed in the bitmaps).
+// With glog, cls[3*seg + g] += #{d : log eps_d = g} for g = 0, 1, 2 (the
+// class of eps_d in F_4* = {1, omega, omega^2}).
 __global__ void __launch_bounds__(256) k_count(const Tile *__restrict__ tiles,
                                                const uint32_t *__restrict__ flags,
                                                const uint32_t *__restrict__ sqfree,
-                                               unsigned long long *__restrict__ counts) {
+                                               unsigned long long *__restrict__ counts,
+                                               const uint8_t *__restrict__ glog,
+                                               unsigned long long *__restrict__ cls) {
     __shared__ uint32_t red[32];
     const Tile t = tiles[blockIdx.x];
     const uint32_t nw = (t.ncand + 31) >> 5;
@@ -196,6 +231,20 @@ __global__ void __launch_bounds__(256) k_count(const Tile *__restrict__ tiles,
     if (threadIdx.x == 0) {
         atomicAdd(&counts[2 * t.seg], (unsigned long long)e);
         atomicAdd(&counts[2 * t.seg + 1], (unsigned long long)dd);
+    }
+    if (glog && cls) {
+        uint32_t c[3] = {0, 0, 0};
+        for (uint32_t k = threadIdx.x; k < t.ncand; k += blockDim.x) {
+            const uint32_t v = glog[t.cand0 + k];
+            c[0] += (v == 1);
+            c[1] += (v == 2);
+            c[2] += (v == 3);
+        }
+        for (int g = 0; g < 3; ++g) {
+            __syncthreads();
+            const uint32_t sum = block_sum(c[g], red);
+            if (threadIdx.x == 0) atomicAdd(&cls[3 * t.seg + g], (unsigned long long)sum);
+        }
     }
 }
 

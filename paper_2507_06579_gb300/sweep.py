@@ -95,8 +95,8 @@ def run_sweep(count_fn: CountFn, blocks: Iterable[Tuple[int, int]], journal: Jou
     for i in range(0, len(todo), batch):
         chunk = todo[i:i + batch]
         res = count_fn(chunk)
-        for blk, (nD, nE) in zip(chunk, res):
-            journal.add(blk, nD, nE)
+        for blk, r in zip(chunk, res):
+            journal.add(blk, r[0], r[1], {"cls": r[2]} if len(r) > 2 else None)
         if on_batch:
             on_batch(i + len(chunk))
     tD = tE = 0
@@ -148,20 +148,47 @@ def fit_five_sixths(curve: Sequence[Tuple[int, int, int]], x_min: float = 1e8) -
     return num / den if den else float("nan")
 
 
-def gpu_counter(ctx):
-    """count_fn over the GPU: one plan (one persistent launch) per batch."""
+def fit_prime_coefficient(curve: Sequence[Tuple[int, int, int]], x_min: float = 1e8) -> float:
+    """Least-squares c in pi_{E cap P}(x) ~ pi(x)/12 + c Li_{1/6}(x), with
+    Li_{1/6}(x) = int_2^x dt / (t^(1/6) log t) (Section 3.2 reports c ~ -0.037).
+    pi(x)/12 is taken as pi_{P, 5 mod 8}(x)/3 from the curve itself (primes
+    == 5 mod 8 are a quarter of all primes), and the integral by the
+    trapezoidal rule on a log grid."""
     import numpy as np
+    pts = [(x, p, e) for x, p, e in curve if x >= x_min]
+    if not pts:
+        return float("nan")
+    xs = np.array([float(x) for x, _, _ in pts])
+    grid = np.exp(np.linspace(np.log(2.0), np.log(xs.max()), 200001))
+    f = 1.0 / (grid ** (1 / 6) * np.log(grid))
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(grid))])
+    li = np.interp(xs, grid, cum)
+    resid = np.array([e - p / 3.0 for _, p, e in pts])
+    return float((resid * li).sum() / (li * li).sum())
+
+
+def gpu_counter(ctx, primes: bool = False, classes: bool = False):
+    """count_fn over the GPU: one plan (one persistent launch) per batch.
+    primes: count the prime d only (pi_{E cap P}, Section 3.2); classes: also
+    return the class counts of eps_d in F_4* as a third element."""
+    import numpy as np
+    import paper_2507_06579_gb300 as E
+
+    flags = (E.EIS_PLAN_PRIMES if primes else 0) | (E.EIS_PLAN_CLASSES if classes else 0)
 
     def count(chunk):
         lo = np.array([a for a, _ in chunk], dtype=np.uint64)
         hi = np.array([b for _, b in chunk], dtype=np.uint64)
-        plan = ctx.plan_create(lo, hi)
+        plan = ctx.plan_create(lo, hi, E.EIS_MODE_PERSISTENT, flags)
         try:
             plan.launch()
             nE = plan.counts()
             nD = plan.counts_D()
+            cls = plan.class_counts() if classes else None
         finally:
             plan.destroy()
+        if classes:
+            return [(int(a), int(b), [int(x) for x in c]) for a, b, c in zip(nD, nE, cls)]
         return [(int(a), int(b)) for a, b in zip(nD, nE)]
 
     return count
@@ -174,6 +201,10 @@ def main(argv=None):
     ap.add_argument("--journal", default=None)
     ap.add_argument("--curve", default=None, help="write (x, pi_D, pi_E) rows here")
     ap.add_argument("--batch", type=int, default=64, help="blocks per plan launch")
+    ap.add_argument("--primes", action="store_true",
+                    help="prime d only: pi_{E cap P} (Section 3.2)")
+    ap.add_argument("--classes", action="store_true",
+                    help="also count the class of eps_d in F_4* per block")
     args = ap.parse_args(argv)
     import torch
     import torch.distributed as dist
@@ -194,15 +225,25 @@ def main(argv=None):
     E.build()
     t0 = time.time()
     with E.Context(local) as ctx:
-        tD, tE = run_sweep(gpu_counter(ctx), mine, journal, batch=args.batch)
+        tD, tE = run_sweep(gpu_counter(ctx, args.primes, args.classes), mine, journal,
+                           batch=args.batch)
     dt = time.time() - t0
     tD, tE = all_reduce_sum([tD, tE])
     if rank == 0:
         out = {"lo": lo, "hi": hi - 1, "pi_D": tD, "pi_E": tE, "blocks": len(blocks),
-               "ranks": world, "seconds_rank0": dt}
-        if world == 1:
+               "ranks": world, "seconds_rank0": dt, "primes_only": bool(args.primes)}
+        if args.classes and world == 1:
+            cls = [0, 0, 0]
+            for b in mine:
+                for g, v in enumerate(journal.rows[b].get("cls", [0, 0, 0])):
+                    cls[g] += v
+            out["classes"] = cls
+        if world == 1 and not args.primes:
             curve = pi_E_curve(journal, lo)
             out["fit_c_5_6"] = fit_five_sixths(curve)
+        if world == 1 and args.primes:
+            curve = pi_E_curve(journal, lo)
+            out["fit_c_prime"] = fit_prime_coefficient(curve)
             if args.curve:
                 with open(args.curve, "w") as f:
                     for x, cD, cE in curve:

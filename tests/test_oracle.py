@@ -247,3 +247,29 @@ def test_table1_pi_E_1e8(orc):
     nD, nE, _ = orc.count_range(0, 10**8 + 1)
     assert nE == iv["total"]
     assert nD == count_D_mobius(0, 10**8 + 1)
+
+
+# ---------------------------------------------------------------- primes (Section 3.2)
+
+def test_is_prime_matches_sympy(orc):
+    sympy = pytest.importorskip("sympy")
+    rng = random.Random(8)
+    vals = list(range(0, 3000)) + [rng.randrange(1, 10**12) for _ in range(300)]
+    for n in vals:
+        assert orc.is_prime(n) == bool(sympy.isprime(n)), n
+
+
+def test_prime_candidates_match_library_sieve(orc):
+    sympy = pytest.importorskip("sympy")
+    lo, hi = 0, 2 * 10**6
+    ps = [p for p in sympy.sieve.primerange(lo, hi) if p % 8 == 5]
+    out = orc.classify_range_primes(lo, hi)
+    d0 = out["d0"]
+    got = [d0 + 8 * int(k) for k in np.nonzero(out["codes"])[0]]
+    assert got == ps
+    # a prime is in E exactly when the square-free classification says so
+    full = orc.classify_range(lo, hi)["codes"]
+    pc = out["codes"]
+    assert np.array_equal(pc[pc > 0], full[pc > 0])
+    nP, nEP, _ = orc.count_range_primes(lo, hi)
+    assert nP == len(ps) and nEP == int((pc == 2).sum())

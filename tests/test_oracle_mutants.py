@@ -24,10 +24,12 @@ MUTANTS = {
                          "int64_t q = (P + s + 1) / Q;\n        int64_t Pn = q * Q - P;          /*"),
     "period_early_exit": ("} while (Q != 2); /* the first", "} while (Q != 2 && n < 3); /* the first"),
     "f4_drop_yy": ("int y = (x1 & y2) ^ (x2 & y1) ^ yy;", "int y = (x1 & y2) ^ (x2 & y1);"),
-    "sieve_wrong_class": ("if (x % 8 == 5) notsf[(x - dlo) / 8] = 1;",
-                          "if (x % 8 == 1) notsf[(x - dlo) / 8] = 1;"),
-    "sieve_skip_k": ("for (uint64_t k = 2; k <= dhi / k; k++) {\n            uint64_t k2",
-                     "for (uint64_t k = 2; k <= dhi / k; k += 2) {\n            uint64_t k2"),
+    "sieve_wrong_class": ("for (; x <= dhi; x += k2) {\n                    if (x % 8 == 5)",
+                          "for (; x <= dhi; x += k2) {\n                    if (x % 8 == 1)"),
+    "sieve_skip_k": ("for (uint64_t k = 2; k <= dhi / k; k++) {\n            if (J->primes)",
+                     "for (uint64_t k = 2; k <= dhi / k; k += 2) {\n            if (J->primes)"),
+    "prime_marks_k_itself": ("if (x < k * k) x = k * k;", "if (x < k) x = k;"),
+    "prime_step_k2": ("for (; x <= dhi; x += k) {", "for (; x <= dhi; x += k * k) {"),
     "unitA_old_P": ("bn_lincomb(&Xn, &X, (uint64_t)Pn, &Y, d)", "bn_lincomb(&Xn, &X, (uint64_t)P, &Y, d)"),
     "unitA_flag_coord": ("int u_par = u.n ? (int)(u.w[0] & 1) : 0;", "int u_par = x_par;"),
     "forms_rho_sign": ("int64_t bp = r - (((r + b) % m) + m) % m;", "int64_t bp = r - (((r - b) % m) + m) % m;"),
@@ -62,6 +64,13 @@ try:
             check("iv%%d" %% d, h4 == (3 * h1 if th == 1 else h1))
     _, nD = orc.sqfree_range(0, 10**5)
     check("mobius", nD == count_D_mobius(0, 10**5))
+    sieve = bytearray([1]) * 100000
+    sieve[0] = sieve[1] = 0
+    for i in range(2, 317):
+        if sieve[i]:
+            sieve[i * i::i] = bytearray(len(sieve[i * i::i]))
+    nP = sum(1 for i in range(5, 100000, 8) if sieve[i])
+    check("primes", orc.count_range_primes(0, 10**5)[0] == nP)
     nD, nE, _ = orc.count_range(0, 10**6 + 1)
     fit = 1e6 / (3 * math.pi**2) - 0.024 * 1e6 ** (5 / 6)
     check("fit", abs(nE - fit) / fit < 0.02)
