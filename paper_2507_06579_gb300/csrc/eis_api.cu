@@ -37,6 +37,7 @@ struct eis_ctx {
     uint64_t budget = 0;
     uint64_t in_use = 0;
     uint32_t *d_primes = nullptr;
+    uint64_t *d_sqtab = nullptr;  // per odd prime p: (p^2)^(-1) mod 2^64, floor((2^64-1)/p^2)
     uint32_t nprimes = 0;
     int *d_single = nullptr;  // [0] result, [1] steps, [2] status
     unsigned char *d_query = nullptr;  // K3 single query: u64 d, i8 out, int status, u64 acc[2], u32 next
@@ -195,7 +196,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                 const size_t smem = (size_t)8 << p->giant_log2n;
                 k_giant<<<p->giant_grid, 32, smem, s>>>(
                     nullptr, p->d_segs, nseg, p->d_defer, p->d_ctr + 2, p->defer_cap,
-                    p->d_ctr + 3, c->d_primes, c->nprimes, nullptr, p->d_flags, p->d_glog,
+                    p->d_ctr + 3, c->d_primes, c->d_sqtab, c->nprimes, nullptr, p->d_flags, p->d_glog,
                     p->d_steps + 1, p->d_status, p->giant_nbaby, p->giant_log2n, kGiantMaxRounds);
                 ++launches;
             }
@@ -486,6 +487,7 @@ eis_ctx_view eis_ctx_get_view(eis_ctx *c) {
     eis_ctx_view v;
     v.device = c->device;
     v.d_primes = c->d_primes;
+    v.d_sqtab = c->d_sqtab;
     v.nprimes = c->nprimes;
     const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : c->occ_persistent;
     v.walk_grid = (uint32_t)(c->sm_count * std::max(1, per_sm));
@@ -561,6 +563,24 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
         eis_destroy(c);
         return EIS_ENOMEM;
     }
+    // Division-free square-free test table (Granlund & Montgomery, section 9):
+    // for odd m = p^2, m | d iff d * m^(-1) mod 2^64 <= floor((2^64-1)/m).
+    {
+        std::vector<uint64_t> tab(2 * pr.size());
+        for (size_t i = 0; i < pr.size(); ++i) {
+            const uint64_t m = (uint64_t)pr[i] * pr[i];
+            uint64_t x = m;  // m * m == 1 (mod 8)
+            for (int k = 0; k < 5; ++k) x *= 2 - m * x;
+            tab[2 * i] = x;
+            tab[2 * i + 1] = UINT64_MAX / m;
+        }
+        if (cudaMalloc(&c->d_sqtab, tab.size() * 8) != cudaSuccess ||
+            cudaMemcpy(c->d_sqtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+            eis_destroy(c);
+            return EIS_ENOMEM;
+        }
+        c->in_use += tab.size() * 8;
+    }
     if (cudaMalloc(&c->d_query, 64) != cudaSuccess) {
         eis_destroy(c);
         return EIS_ENOMEM;
@@ -590,6 +610,7 @@ int eis_destroy(eis_ctx *c) {
     if (c->d_primes) cudaFree(c->d_primes);
     if (c->d_single) cudaFree(c->d_single);
     if (c->d_query) cudaFree(c->d_query);
+    if (c->d_sqtab) cudaFree(c->d_sqtab);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return EIS_OK;
@@ -932,7 +953,7 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
     if (c->mode == EIS_MODE_PLAIN) {
         // one lane walks the half period
         EIS_CK(cudaMemsetAsync(c->d_single, 0, 4 * sizeof(int), c->stream));
-        k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->nprimes, c->d_single,
+        k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->d_sqtab, c->nprimes, c->d_single,
                                                c->d_single + 2, limit);
         EIS_CK(cudaGetLastError());
         int h[4] = {0, 0, 0, 0};
@@ -951,7 +972,7 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
         EIS_CK(cudaMemcpyAsync(q, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
         k_giant<<<1, 32, (size_t)8 << log2n, c->stream>>>(
             reinterpret_cast<const uint64_t *>(q), nullptr, 0, nullptr, nullptr, 1,
-            reinterpret_cast<uint32_t *>(q + 32), c->d_primes, c->nprimes,
+            reinterpret_cast<uint32_t *>(q + 32), c->d_primes, c->d_sqtab, c->nprimes,
             reinterpret_cast<int8_t *>(q + 8), nullptr, nullptr,
             reinterpret_cast<unsigned long long *>(q + 16), reinterpret_cast<int *>(q + 12), nbaby,
             log2n, kGiantMaxRounds);

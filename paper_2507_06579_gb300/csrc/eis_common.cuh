@@ -81,6 +81,29 @@ __device__ __forceinline__ uint64_t isqrt_u64(uint64_t d) {
     return s;
 }
 
+// Square-free test of one d (d == 5 mod 8, d < 2^44) by one warp, without
+// division: for odd m, m | d iff d * m^(-1) mod 2^64 <= floor((2^64-1)/m)
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, section 9).  sqtab[2i] = (p_i^2)^(-1) mod 2^64,
+// sqtab[2i+1] = floor((2^64-1)/p_i^2) for the odd primes p_i (ascending);
+// the primes with p^2 <= d are found by binary search.
+__device__ __forceinline__ bool warp_squarefree_fast(uint64_t d, const uint32_t *__restrict__ primes,
+                                                     const uint64_t *__restrict__ sqtab,
+                                                     uint32_t nprimes) {
+    uint32_t lo = 0, hi = nprimes;  // count of primes with p^2 <= d
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint64_t p = primes[mid];
+        if (p * p <= d) lo = mid + 1; else hi = mid;
+    }
+    bool hit = false;
+    for (uint32_t i = threadIdx.x & 31; i < lo; i += 32) {
+        const uint64_t inv = sqtab[2 * i], lim = sqtab[2 * i + 1];
+        hit |= d * inv <= lim;
+    }
+    return !__any_sync(0xffffffffu, hit);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

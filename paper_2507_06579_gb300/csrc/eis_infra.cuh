@@ -35,8 +35,31 @@ struct Ideal {
     int g;      // generator class in Z/3
 };
 
+// Extended Euclid in 32-bit arithmetic for 0 <= a, b < 2^31 (the ideal norms
+// and their half-sums are below 2^23): returns gcd with x a + y b = gcd.
+__device__ __forceinline__ int64_t egcd32(int32_t a, int32_t b, int64_t &x, int64_t &y) {
+    int32_t x0 = 1, y0 = 0, x1 = 0, y1 = 1;
+    while (b != 0) {
+        const int32_t q = a / b;
+        int32_t t = a - q * b;
+        a = b;
+        b = t;
+        t = x0 - q * x1;
+        x0 = x1;
+        x1 = t;
+        t = y0 - q * y1;
+        y0 = y1;
+        y1 = t;
+    }
+    x = x0;
+    y = y0;
+    return a;
+}
+
 // Extended Euclid: returns gcd(a, b) >= 0 with x a + y b = gcd.
 __device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t &x, int64_t &y) {
+    if (a >= 0 && b >= 0 && a < 0x7fffffff && b < 0x7fffffff)
+        return egcd32((int32_t)a, (int32_t)b, x, y);
     int64_t x0 = 1, y0 = 0, x1 = 0, y1 = 1;
     while (b != 0) {
         const int64_t q = a / b;

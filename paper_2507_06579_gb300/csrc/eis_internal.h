@@ -9,6 +9,7 @@
 struct eis_ctx_view {
     int device;
     const uint32_t *d_primes;  // odd primes < 2^22 on the device
+    const uint64_t *d_sqtab;   // their division-free square-divisibility table
     uint32_t nprimes;
     uint32_t walk_grid;        // persistent walk grid (SMs x resident CTAs)
     uint32_t giant_grid;       // one-warp blocks of k_giant that fit at once (SMs x 4)

@@ -30,10 +30,11 @@ __global__ void k_walk_persistent(const Seg *segs, uint32_t nseg, const uint32_t
                                   uint32_t *defer_count, uint32_t defer_cap, int fast);
 __global__ void k_giant(const uint64_t *ds, const Seg *segs, uint32_t nseg, const uint32_t *cands,
                         const uint32_t *n_ptr, uint32_t n_fixed, uint32_t *next_ptr,
-                        const uint32_t *primes, uint32_t nprimes, int8_t *out_g, uint32_t *flags,
+                        const uint32_t *primes, const uint64_t *sqtab, uint32_t nprimes,
+                        int8_t *out_g, uint32_t *flags,
                         uint8_t *glog, unsigned long long *acc, int *status, int nbaby, int log2n,
                         uint32_t max_rounds);
-__global__ void k_walk_single(uint64_t d, const uint32_t *primes, uint32_t nprimes, int *out,
-                              int *status, uint32_t step_limit);
+__global__ void k_walk_single(uint64_t d, const uint32_t *primes, const uint64_t *sqtab,
+                              uint32_t nprimes, int *out, int *status, uint32_t step_limit);
 
 }  // namespace eis

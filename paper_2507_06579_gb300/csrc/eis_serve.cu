@@ -204,7 +204,7 @@ bool launch_batch(eis_server *s, Slot &sl) {
             eis_giant_params(dmax, 0, nbaby, log2n);
             k_giant<<<s->giant_grid, 32, (size_t)8 << log2n, st>>>(
                 nullptr, sl.d_segs, nseg, sl.d_defer, sl.d_ctr + 2, s->defer_cap, sl.d_ctr + 3,
-                cv.d_primes, cv.nprimes, nullptr, sl.d_flags, nullptr, sl.d_steps + 1,
+                cv.d_primes, cv.d_sqtab, cv.nprimes, nullptr, sl.d_flags, nullptr, sl.d_steps + 1,
                 sl.d_status, nbaby, log2n, 1u << 20);
         }
         k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts, nullptr,
@@ -223,7 +223,8 @@ bool launch_batch(eis_server *s, Slot &sl) {
         cudaMemsetAsync(sl.d_mem_ctl, 0, 64, st);
         k_giant<<<std::min<uint32_t>(nmem, s->giant_grid), 32, (size_t)8 << log2n, st>>>(
             sl.d_mem_d, nullptr, 0, nullptr, nullptr, nmem,
-            reinterpret_cast<uint32_t *>(sl.d_mem_ctl), cv.d_primes, cv.nprimes, sl.d_mem_out,
+            reinterpret_cast<uint32_t *>(sl.d_mem_ctl), cv.d_primes, cv.d_sqtab, cv.nprimes,
+            sl.d_mem_out,
             nullptr, nullptr, reinterpret_cast<unsigned long long *>(sl.d_mem_ctl + 8),
             reinterpret_cast<int *>(sl.d_mem_ctl + 24), nbaby, log2n, 1u << 20);
         cudaMemcpyAsync(sl.h_mem_out, sl.d_mem_out, nmem, cudaMemcpyDeviceToHost, st);

@@ -152,23 +152,12 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
     return res;  // no hit within max_rounds: error
 }
 
-__device__ __forceinline__ bool warp_squarefree(uint64_t d, const uint32_t *__restrict__ primes,
-                                                uint32_t nprimes) {
-    bool hit = false;
-    for (uint32_t i = threadIdx.x & 31; i < nprimes; i += 32) {
-        const uint64_t p = primes[i];
-        if (p * p > d) break;
-        if (d % (p * p) == 0) hit = true;
-    }
-    return !__any_sync(kFull, hit);
-}
-
 }  // namespace
 
 // One warp per item; items are taken from a global counter.
 //   ds != nullptr : item i is d = ds[i]; out_g[i] = 0 (not in D),
 //                   1 + log eps_d, or -1 (error); the square-free test runs
-//                   against the prime table.
+//                   against the prime table (division-free, eis_common.cuh).
 //   ds == nullptr : item i is candidate cands[i] of the Seg layout (already
 //                   square-free); its flag bit / log byte are written.
 // Dynamic shared memory: (blockDim.x / 32) tables of 2^log2n uint64.
@@ -177,7 +166,8 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
                                                const uint32_t *__restrict__ cands,
                                                const uint32_t *__restrict__ n_ptr, uint32_t n_fixed,
                                                uint32_t *__restrict__ next_ptr,
-                                               const uint32_t *__restrict__ primes, uint32_t nprimes,
+                                               const uint32_t *__restrict__ primes,
+                                               const uint64_t *__restrict__ sqtab, uint32_t nprimes,
                                                int8_t *__restrict__ out_g,
                                                uint32_t *__restrict__ flags,
                                                uint8_t *__restrict__ glog,
@@ -196,7 +186,7 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
         if (item >= n) break;
         if (ds) {
             const uint64_t d = ds[item];
-            if (d % 8 != 5 || !warp_squarefree(d, primes, nprimes)) {
+            if (d % 8 != 5 || !warp_squarefree_fast(d, primes, sqtab, nprimes)) {
                 if (lane == 0) out_g[item] = 0;
                 continue;
             }

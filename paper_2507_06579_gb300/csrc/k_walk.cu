@@ -198,15 +198,10 @@ __global__ void __launch_bounds__(256) k_walk_persistent(
 // 1 + log eps_d; out[1] = steps.  The square-free test covers every odd prime
 // p with p^2 <= d from the table (d < 2^44 needs p < 2^22).
 __global__ void __launch_bounds__(32) k_walk_single(uint64_t d, const uint32_t *__restrict__ primes,
+                                                    const uint64_t *__restrict__ sqtab,
                                                     uint32_t nprimes, int *__restrict__ out,
                                                     int *__restrict__ status, uint32_t step_limit) {
-    bool hit = false;
-    for (uint32_t i = threadIdx.x; i < nprimes; i += 32) {
-        const uint64_t p = primes[i];
-        if (p * p > d) break;
-        if (d % (p * p) == 0) hit = true;
-    }
-    const bool sq = !__any_sync(kFull, hit);
+    const bool sq = warp_squarefree_fast(d, primes, sqtab, nprimes);
     if (threadIdx.x != 0) return;
     if (!sq || d % 8 != 5) {
         out[0] = 0;
