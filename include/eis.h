@@ -301,6 +301,8 @@ typedef struct {
                               /* warp-per-d giant-step kernel (131072); this  */
                               /* cuts the latency of batches holding a very   */
                               /* long period; 0xffffffff: never               */
+    uint32_t giant_max;       /* at most this many walks per batch go to the     */
+                              /* giant-step kernel (0: slot_candidates / 8)      */
 } eis_server_config;
 
 typedef struct {

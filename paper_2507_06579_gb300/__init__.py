@@ -105,7 +105,7 @@ class TuneResult(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("slot_candidates", ctypes.c_uint64),
                 ("slot_requests", ctypes.c_uint32), ("max_pending", ctypes.c_uint32),
-                ("giant_after", ctypes.c_uint32)]
+                ("giant_after", ctypes.c_uint32), ("giant_max", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -274,9 +274,11 @@ class Server:
     """Continuous-batching request server (eis_server_*)."""
 
     def __init__(self, ctx: "Context", slots: int = 0, slot_candidates: int = 0,
-                 slot_requests: int = 0, max_pending: int = 0, giant_after: int = 0):
+                 slot_requests: int = 0, max_pending: int = 0, giant_after: int = 0,
+                 giant_max: int = 0):
         self.ctx = ctx
-        cfg = ServerConfig(slots, slot_candidates, slot_requests, max_pending, giant_after)
+        cfg = ServerConfig(slots, slot_candidates, slot_requests, max_pending, giant_after,
+                           giant_max)
         h = ctypes.c_void_p()
         _check(lib().eis_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)),
                "eis_server_create")

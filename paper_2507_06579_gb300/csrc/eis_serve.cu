@@ -384,6 +384,7 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
         if (cfg->slot_requests) c.slot_requests = cfg->slot_requests;
         if (cfg->max_pending) c.max_pending = cfg->max_pending;
         c.giant_after = cfg->giant_after;
+        c.giant_max = cfg->giant_max;
     }
     if (c.giant_after == 0) c.giant_after = 131072;
     if (c.slots > 64 || c.slot_candidates < 64 || c.slot_candidates > ((uint64_t)1 << 30) ||
@@ -397,10 +398,14 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
     s->cfg = c;
     s->max_tiles = (uint32_t)(c.slot_candidates / kTileCands) + c.slot_requests + 1;
     s->grid = v.walk_grid;
-    s->defer_after = c.giant_after == 0xffffffffu ? 0u : c.giant_after;
     s->giant_grid = v.giant_grid;
+    s->defer_after = c.giant_after == 0xffffffffu ? 0u : c.giant_after;
     s->step_limit = v.step_limit;
-    s->defer_cap = (uint32_t)std::max<uint64_t>(1024, c.slot_candidates / 8);
+    // At most giant_max walks of a batch go to the giant-step kernel (default:
+    // an eighth of a slot, in practice every walk past giant_after; capping
+    // lower measured no better at p99).
+    s->defer_cap = c.giant_max ? c.giant_max
+                               : (uint32_t)std::max<uint64_t>(1024, c.slot_candidates / 8);
     const uint64_t need = slot_bytes(c, s->max_tiles, s->defer_cap) * c.slots;
     if (!eis_ctx_reserve(ctx, need)) {
         delete s;
