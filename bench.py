@@ -350,12 +350,25 @@ def main():
     if args.serve_seconds > 0 and rank == 0:
         rng = np.random.default_rng(6)
         ds = [int(x) * 8 + 5 for x in rng.integers(10**12 // 8 - 10**9, 10**12 // 8, size=400)]
+        top = E.EIS_D_LIMIT // 8
+        ds44 = [int(x) * 8 + 5 for x in rng.integers(top - 10**9, top, size=100)]
         membership = {"workload": "400 random d == 5 mod 8 in [1e12 - 8e9, 1e12] (not-square-free "
-                                  "d included: they return EIS_ENOTD)"}
-        for name, mode in (("giant", E.EIS_MODE_PERSISTENT), ("plain", E.EIS_MODE_PLAIN)):
+                                  "d included: they return EIS_ENOTD); *_2^44: 100 more just "
+                                  "below 2^44",
+                      "giant": "giant steps by textbook composition + rho (default)",
+                      "giant_nucomp": "giant steps by NUCOMP/NUDUPL (Algorithms 2-4)",
+                      "plain": "single-lane walk of the half period"}
+        for name, mode, comp, dset in (
+                ("giant", E.EIS_MODE_PERSISTENT, E.EIS_COMPOSE_TEXTBOOK, ds),
+                ("giant_nucomp", E.EIS_MODE_PERSISTENT, E.EIS_COMPOSE_NUCOMP, ds),
+                ("plain", E.EIS_MODE_PLAIN, E.EIS_COMPOSE_TEXTBOOK, ds),
+                ("giant_2^44", E.EIS_MODE_PERSISTENT, E.EIS_COMPOSE_TEXTBOOK, ds44),
+                ("giant_nucomp_2^44", E.EIS_MODE_PERSISTENT, E.EIS_COMPOSE_NUCOMP, ds44),
+                ("plain_2^44", E.EIS_MODE_PLAIN, E.EIS_COMPOSE_TEXTBOOK, ds44[:20])):
             ctx.set_option(E.EIS_OPT_MODE, mode)
+            ctx.set_option(E.EIS_OPT_GIANT_COMPOSE, comp)
             lat = []
-            for d in ds:
+            for d in dset:
                 t1 = time.perf_counter()
                 try:
                     ctx.is_eisenstein(d)
@@ -365,8 +378,9 @@ def main():
             lat = np.array(lat)
             membership[name] = {"p50_ms": float(np.percentile(lat, 50)),
                                 "p99_ms": float(np.percentile(lat, 99)),
-                                "max_ms": float(lat.max())}
+                                "max_ms": float(lat.max()), "n": len(dset)}
         ctx.set_option(E.EIS_OPT_MODE, E.EIS_MODE_PERSISTENT)
+        ctx.set_option(E.EIS_OPT_GIANT_COMPOSE, E.EIS_COMPOSE_TEXTBOOK)
 
     # end to end through the public call with host buffers
     n_cand, _ = E.num_candidates(lo, hi)

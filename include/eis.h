@@ -77,6 +77,13 @@ extern "C" {
 #define EIS_OPT_GIANT_THRESHOLD 6 /* baby steps after which a d is handed to  */
                                   /* the giant-step kernel (0 = never)        */
 #define EIS_OPT_GIANT_STRIDE 7   /* giant-step stride in baby steps (0: auto) */
+#define EIS_OPT_GIANT_COMPOSE 8  /* giant-step composition: EIS_COMPOSE_*      */
+
+/* Giant-step compositions (EIS_OPT_GIANT_COMPOSE). */
+#define EIS_COMPOSE_TEXTBOOK 0 /* product of forms, then rho until reduced      */
+                               /* (default: measured slightly faster below 2^44)*/
+#define EIS_COMPOSE_NUCOMP 1   /* NUCOMP / NUDUPL / NUCOMPchoose (Algorithms    */
+                               /* 2-4): near-reduced output, ~1 rho step after  */
 
 typedef struct eis_ctx eis_ctx;
 typedef struct eis_plan eis_plan;

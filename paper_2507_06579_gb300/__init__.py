@@ -62,6 +62,9 @@ EIS_OPT_STEP_LIMIT = 4
 EIS_OPT_USE_GRAPH = 5
 EIS_OPT_GIANT_THRESHOLD = 6
 EIS_OPT_GIANT_STRIDE = 7
+EIS_OPT_GIANT_COMPOSE = 8
+EIS_COMPOSE_TEXTBOOK = 0
+EIS_COMPOSE_NUCOMP = 1
 
 _lock = threading.Lock()
 _lib = None

@@ -48,6 +48,7 @@ struct eis_ctx {
     int use_graph = 1;
     int64_t giant_threshold = 0;
     int64_t giant_stride = 0;
+    int giant_compose = EIS_COMPOSE_TEXTBOOK;
     int occ_persistent = 1;
     eis_stats last{};
 };
@@ -197,7 +198,8 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                 k_giant<<<p->giant_grid, 32, smem, s>>>(
                     nullptr, p->d_segs, nseg, p->d_defer, p->d_ctr + 2, p->defer_cap,
                     p->d_ctr + 3, c->d_primes, c->d_sqtab, c->nprimes, nullptr, p->d_flags, p->d_glog,
-                    p->d_steps + 1, p->d_status, p->giant_nbaby, p->giant_log2n, kGiantMaxRounds);
+                    p->d_steps + 1, p->d_status, p->giant_nbaby, p->giant_log2n, kGiantMaxRounds,
+                    c->giant_compose);
                 ++launches;
             }
             record(p->ev[4], s, capturing);
@@ -492,6 +494,7 @@ eis_ctx_view eis_ctx_get_view(eis_ctx *c) {
     const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : c->occ_persistent;
     v.walk_grid = (uint32_t)(c->sm_count * std::max(1, per_sm));
     v.giant_grid = (uint32_t)(c->sm_count * 4);
+    v.giant_compose = c->giant_compose;
     v.step_limit = (uint32_t)std::min<int64_t>(c->step_limit, 0xffffffffll);
     return v;
 }
@@ -646,6 +649,10 @@ int eis_set_option(eis_ctx *c, int key, int64_t v) {
             if (v < 0) return EIS_EINVAL;
             c->giant_stride = v;
             return EIS_OK;
+        case EIS_OPT_GIANT_COMPOSE:
+            if (v != EIS_COMPOSE_TEXTBOOK && v != EIS_COMPOSE_NUCOMP) return EIS_EINVAL;
+            c->giant_compose = (int)v;
+            return EIS_OK;
         default:
             return EIS_EINVAL;
     }
@@ -661,6 +668,7 @@ int eis_get_option(eis_ctx *c, int key, int64_t *v) {
         case EIS_OPT_USE_GRAPH: *v = c->use_graph; return EIS_OK;
         case EIS_OPT_GIANT_THRESHOLD: *v = c->giant_threshold; return EIS_OK;
         case EIS_OPT_GIANT_STRIDE: *v = c->giant_stride; return EIS_OK;
+        case EIS_OPT_GIANT_COMPOSE: *v = c->giant_compose; return EIS_OK;
         default: return EIS_EINVAL;
     }
 }
@@ -975,7 +983,7 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
             reinterpret_cast<uint32_t *>(q + 32), c->d_primes, c->d_sqtab, c->nprimes,
             reinterpret_cast<int8_t *>(q + 8), nullptr, nullptr,
             reinterpret_cast<unsigned long long *>(q + 16), reinterpret_cast<int *>(q + 12), nbaby,
-            log2n, kGiantMaxRounds);
+            log2n, kGiantMaxRounds, c->giant_compose);
         EIS_CK(cudaGetLastError());
         unsigned char h[64];
         EIS_CK(cudaMemcpyAsync(h, q, 64, cudaMemcpyDeviceToHost, c->stream));

@@ -182,6 +182,209 @@ __device__ __forceinline__ bool ideal_mul(const Ideal &X, const Ideal &Y, int64_
     return true;
 }
 
+// ---------------------------------------------------------------- NUCOMP
+// Algorithms 2-4 (NUCOMP, NUDUPL, NUCOMPchoose) on forms (u, v, w) with
+// v^2 - 4uw = d; the ideal [Q/2, (P+sqrt d)/2] is the form (Q/2, -P, w),
+// w = (P^2 - d)/(2Q).  The output ideal I = (1/gamma) I1 I2 is near-reduced,
+// so one or two rho steps finish the reduction.  Its generator class is
+// g1 + g2 - log(gamma mod 2O_K): gamma = (A + B sqrt d)/C is a unit at 2
+// (Appendix A: 1/gamma = theta/(theta' theta'') with all three outside 2O_K);
+// gamma C = (A - B) + 2B omega, and after dividing both coordinates by their
+// common power of two (which equals the power of two in C) the parities give
+// gamma mod 2O_K.  Only those low bits are needed, so A, B, C are formed in
+// wrapping 64-bit arithmetic.
+
+// log_omega of (x + y omega) for (x, y) != (0, 0) mod 2.
+__device__ __forceinline__ int f4_log(int x, int y) { return y ? (x ? 2 : 1) : 0; }
+
+__device__ __forceinline__ int gamma_class(uint64_t A, uint64_t B, uint64_t C, bool &ok) {
+    const uint64_t a = A - B, b = 2 * B;
+    const int ka = a ? __ffsll((long long)a) - 1 : 64;
+    const int kb = b ? __ffsll((long long)b) - 1 : 64;
+    const int k = ka < kb ? ka : kb;
+    const int kc = C ? __ffsll((long long)C) - 1 : 64;
+    if (k != kc || k >= 63) {
+        ok = false;
+        return 0;
+    }
+    return f4_log((int)((a >> k) & 1), (int)((b >> k) & 1));
+}
+
+// Partial Euclid of NUCOMP/NUDUPL: stops once |by| <= L or bx = 0.
+__device__ __forceinline__ void nu_partial(int64_t &bx, int64_t &by, int64_t &x, int64_t &y,
+                                           int &z, int64_t L) {
+    x = 1;
+    y = 0;
+    z = 0;
+    while ((by < 0 ? -by : by) > L && bx != 0) {
+        const int64_t q = by / bx, t = by - q * bx;  // bx, by >= 0 here
+        by = bx;
+        bx = t;
+        const int64_t u = y - q * x;
+        y = x;
+        x = u;
+        ++z;
+    }
+    if (z & 1) {
+        by = -by;
+        y = -y;
+    }
+}
+
+// NUCOMP (Algorithm 2).  Returns false if a division that must be exact is
+// not (never expected).
+__device__ __forceinline__ bool nucomp(int64_t u1, int64_t v1, int64_t w1, int64_t u2, int64_t v2,
+                                       int64_t w2, int64_t L, int64_t &u3, int64_t &v3,
+                                       int64_t &w3, uint64_t &A, uint64_t &B, uint64_t &C) {
+    if (w1 < w2) {
+        int64_t t = u1; u1 = u2; u2 = t;
+        t = v1; v1 = v2; v2 = t;
+        t = w1; w1 = w2; w2 = t;
+    }
+    const int64_t s = (v1 + v2) / 2, m = v2 - s;
+    int64_t b, c;
+    const int64_t F = egcd64(u2, u1, b, c);  // b u2 + c u1 = F
+    int64_t G, Bx, By, Cy, Dy;
+    if (s % F == 0) {
+        G = F;
+        Bx = m * b;
+        By = u1 / G;
+        Cy = u2 / G;
+        Dy = s / G;
+    } else {
+        int64_t xx, yy;
+        G = egcd64(F, s, xx, yy);  // xx F + yy s = G
+        const int64_t H = F / G;
+        By = u1 / G;
+        Cy = u2 / G;
+        Dy = s / G;
+        const int64_t l = mod_pos(mod_pos(yy, H) * mod_pos(mod_pos(b, H) * mod_pos(w1, H) +
+                                                        mod_pos(c, H) * mod_pos(w2, H), H), H);
+        const int64_t num = b * m + l * By;
+        if (num % H) return false;
+        Bx = num / H;
+    }
+    int64_t bx = mod_pos(Bx, By), by = By, x, y;
+    int z;
+    nu_partial(bx, by, x, y, z, L);
+    const int64_t ax = G * x, ay = G * y;
+    if (z != 0) {
+        const int64_t n1 = Cy * bx - m * x;
+        if (n1 % By) return false;
+        const int64_t cx = n1 / By;
+        const int64_t Q1 = by * cx, Q2 = Q1 + m;
+        const int64_t n2 = Dy * bx - w2 * x;
+        if (n2 % By) return false;
+        const int64_t dx = n2 / By;
+        const int64_t Q3 = y * dx, Q4 = Q3 + Dy;
+        if (Q4 % x) return false;
+        const int64_t dy = Q4 / x;
+        int64_t cy;
+        if (bx != 0) {
+            if (Q2 % bx) return false;
+            cy = Q2 / bx;
+        } else {
+            const int64_t n3 = cx * dy - w1;
+            if (n3 % dx) return false;
+            cy = n3 / dx;
+        }
+        u3 = by * cy - ay * dy;
+        w3 = bx * cx - ax * dx;
+        v3 = G * (Q3 + Q4) - Q1 - Q2;
+    } else {
+        const int64_t Q1 = Cy * bx;
+        if ((Q1 - m) % By || (bx * Dy - w2) % By) return false;
+        const int64_t cx = (Q1 - m) / By, dx = (bx * Dy - w2) / By;
+        u3 = by * Cy;
+        w3 = bx * cx - G * dx;
+        v3 = v2 - 2 * Q1;
+    }
+    const uint64_t t = 2 * (uint64_t)u3;
+    A = (uint64_t)G * ((uint64_t)x * t + (uint64_t)y * (uint64_t)v3);
+    B = (uint64_t)G * (uint64_t)y;
+    C = t;
+    return true;
+}
+
+// NUDUPL (Algorithm 3).
+__device__ __forceinline__ bool nudupl(int64_t u, int64_t v, int64_t w, int64_t L, int64_t &u3,
+                                       int64_t &v3, int64_t &w3, uint64_t &A, uint64_t &B,
+                                       uint64_t &C) {
+    int64_t xx, yy;
+    const int64_t G = egcd64(u, v, xx, yy);  // xx u + yy v = G
+    const int64_t By = u / G, Dy = v / G;
+    int64_t bx = mod_pos(mod_pos(yy, By) * mod_pos(w, By), By), by = By, x, y;
+    int z;
+    nu_partial(bx, by, x, y, z, L);
+    const int64_t ax = G * x, ay = G * y;
+    if (z == 0) {
+        const int64_t n = bx * Dy - w;
+        if (n % By) return false;
+        const int64_t dx = n / By;
+        u3 = by * by;
+        w3 = bx * bx;
+        v3 = v - (bx + by) * (bx + by) + u3 + w3;
+        w3 = w3 - G * dx;
+    } else {
+        const int64_t n = bx * Dy - w * x;
+        if (n % By) return false;
+        const int64_t dx = n / By;
+        const int64_t Q1 = dx * y;
+        int64_t dy = Q1 + Dy;
+        v3 = G * (dy + Q1);
+        if (dy % x) return false;
+        dy = dy / x;
+        u3 = by * by;
+        w3 = bx * bx;
+        v3 = v3 - (bx + by) * (bx + by) + u3 + w3;
+        u3 = u3 - ay * dy;
+        w3 = w3 - ax * dx;
+    }
+    const uint64_t t = 2 * (uint64_t)u3;
+    A = (uint64_t)G * ((uint64_t)x * t + (uint64_t)y * (uint64_t)v3);
+    B = (uint64_t)G * (uint64_t)y;
+    C = t;
+    return true;
+}
+
+// NUCOMPchoose (Algorithm 4) + reduction: reduce(X * Y) with classes.
+__device__ __forceinline__ bool ideal_mul_nucomp(const Ideal &X, const Ideal &Y, int64_t d,
+                                                 int64_t s, int64_t L, Ideal &out) {
+    int64_t u1 = 2 * X.a, u2 = 2 * Y.a;  // Q (positive for reduced ideals)
+    int64_t v1 = mod_pos(X.b, u1), v2 = mod_pos(Y.b, u2);
+    int64_t P, Q;
+    int lg = 0;
+    if (u1 <= 50 || u2 <= 50) {
+        int64_t a3, b3;
+        ideal_compose(X.a, X.b, Y.a, Y.b, d, a3, b3);  // gamma = content, odd
+        P = b3;
+        Q = 2 * a3;
+    } else {
+        const int64_t w1 = (v1 * v1 - d) / (2 * u1);
+        int64_t u3, v3, w3;
+        uint64_t A, B, C;
+        bool ok;
+        if (u1 == u2 && v1 == v2) {
+            ok = nudupl(u1 / 2, -v1, w1, L, u3, v3, w3, A, B, C);
+        } else {
+            const int64_t w2 = (v2 * v2 - d) / (2 * u2);
+            ok = nucomp(u1 / 2, -v1, w1, u2 / 2, -v2, w2, L, u3, v3, w3, A, B, C);
+        }
+        if (!ok) return false;
+        bool okg = true;
+        lg = gamma_class(A, B, C, okg);
+        if (!okg) return false;
+        Q = 2 * (u3 < 0 ? -u3 : u3);
+        P = mod_pos(-v3, Q);
+    }
+    const int gr = ideal_reduce(P, Q, d, s, 256);
+    if (gr < 0) return false;
+    out.a = Q / 2;
+    out.b = P;
+    out.g = (X.g + Y.g + 3 - lg + gr) % 3;
+    return true;
+}
+
 // ---------------------------------------------------------------- baby table
 // Open-addressing hash in shared memory, one per warp, written by lane 0 only.
 // Entry: key (Q << 24 | P) << 3 | type << 2 | class, 0 = empty.
@@ -206,6 +409,22 @@ __device__ __forceinline__ bool infra_insert(uint64_t *tab, int log2n, uint64_t 
             return true;
         }
         if ((e >> 3) == key) return true;  // already present (same ideal)
+    }
+    return false;
+}
+
+// The same insert for several lanes of a warp at once (compare-and-swap on
+// the slot, so two lanes never claim one empty slot).
+__device__ __forceinline__ bool infra_insert_cas(uint64_t *tab, int log2n, uint64_t key,
+                                                 uint64_t type, int cls) {
+    const uint32_t mask = (1u << log2n) - 1;
+    const unsigned long long val = (key << 3) | (type << 2) | (uint64_t)cls;
+    uint32_t h = infra_hash(key, log2n);
+    for (uint32_t i = 0; i <= mask; ++i, h = (h + 1) & mask) {
+        const unsigned long long e =
+            atomicCAS(reinterpret_cast<unsigned long long *>(tab + h), 0ull, val);
+        if (e == 0) return true;
+        if ((e >> 3) == key) return true;
     }
     return false;
 }

@@ -13,6 +13,7 @@ struct eis_ctx_view {
     uint32_t nprimes;
     uint32_t walk_grid;        // persistent walk grid (SMs x resident CTAs)
     uint32_t giant_grid;       // one-warp blocks of k_giant that fit at once (SMs x 4)
+    int giant_compose;         // EIS_COMPOSE_*
     uint32_t step_limit;
 };
 

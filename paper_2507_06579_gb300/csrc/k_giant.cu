@@ -1,9 +1,12 @@
 // k_giant.cu -- infrastructure baby-step giant-step kernel (Algorithm 1),
 // one warp per discriminant, generator classes in Z/3 (Appendix A).
 //
-// Baby steps: lane 0 walks states j = 1..N from O_K (fp32 walk of
-// eis_common.cuh), stopping early at the centre of a short period.  Each
-// state goes into the warp's shared-memory table twice:
+// Baby steps: all 32 lanes run the same walk from O_K (fp32 walk of
+// eis_common.cuh; it is deterministic, so every lane holds the same state),
+// stopping early at the centre of a short period.  Lane t keeps state j with
+// j = t mod 32 in registers, and after every 32 steps the lanes insert their
+// states at once, so the hash inserts stay off the walk's dependency chain.
+// Each state goes into the warp's shared-memory table twice:
 //   direct  (Q_j, P_j)      -> S_j, the position delta_j of state j;
 //   mirror  (Q_j, P_{j+1})  -> S_j, which is state l - j (the period is
 //                               palindromic), position R - delta_j,
@@ -11,9 +14,10 @@
 // [R - delta_N, R + delta_N] around the regulator R.
 // Giant steps: G = state N+1; lane t starts at G^(t+2) and strides by G^32,
 // so round r looks up positions about (32 r + t + 2) delta_{N+1}.  Every
-// giant step is reduce(G^32 * mu) (eis_infra.cuh).  The stride is shorter than
-// the window, so the first hit in (round, lane) order is the first giant step
-// inside it:
+// giant step is reduce(G^32 * mu) (eis_infra.cuh), by the textbook
+// composition or by NUCOMP/NUDUPL/NUCOMPchoose (Algorithms 2-4).  The stride
+// is shorter than the window, so the first hit in (round, lane) order is the
+// first giant step inside it:
 //   mirror hit on j (position R - delta_j, no wrap): log eps = g(mu) + S_j,
 //     because S_l - S_{l-j} = S_j;
 //   direct hit on j (position R + delta_j, one wrap): log eps = g(mu) - S_j.
@@ -32,12 +36,13 @@ struct GiantOut {
     uint32_t giant;
 };
 
-// Lane 0's baby phase: states 1..N into the table (direct and mirror keys);
-// done = 1 with gres = log eps_d if the centre comes first (or gres = -1 if
-// the table overflowed); otherwise G = state N+1.
+// The baby phase, run by all 32 lanes: states 1..N into the table (direct and
+// mirror keys); done = 1 with gres = log eps_d if the centre comes first (or
+// gres = -1 if the table overflowed); otherwise G = state N+1.  All outputs
+// are the same on every lane.
 template <bool kFast>
 __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n, int nbaby,
-                                           int &done, int &gres, int &nb, int64_t &Ga,
+                                           int lane, int &done, int &gres, int &nb, int64_t &Ga,
                                            int64_t &Gb, int &Gg) {
     WalkState w;
     int g;
@@ -47,13 +52,18 @@ __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n,
         gres = g;
         return;
     }
-    const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
-    bool ok = infra_insert(tab, log2n, infra_key(2, P1), 0, 0);
-    for (int j = 1; j <= nbaby && ok; ++j) {
+    bool ok = true;
+    if (lane == 0) {
+        const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
+        ok = infra_insert_cas(tab, log2n, infra_key(2, P1), 0, 0);
+    }
+    int64_t kQ = 0, kP = 0, kPn = 0;  // the state this lane holds
+    int kS = 0;
+    bool held = false;
+    for (int j = 1; j <= nbaby; ++j) {
         const int64_t Pj = __float_as_int(w.Pm) & 0x7fffff;
         const int64_t Qj = (int64_t)w.Q;
         const int Sj = (w.acc2 >> 1) % 3;
-        ok &= infra_insert(tab, log2n, infra_key(Qj, Pj), 0, Sj);
         const bool centre = walk_step<kFast>(w);
         ++nb;
         if (centre) {
@@ -61,10 +71,23 @@ __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n,
             gres = walk_finish(w);
             return;
         }
-        const int64_t Pn = __float_as_int(w.Pm) & 0x7fffff;
-        ok &= infra_insert(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
+        if ((j & 31) == lane) {
+            kQ = Qj;
+            kP = Pj;
+            kPn = __float_as_int(w.Pm) & 0x7fffff;
+            kS = Sj;
+            held = true;
+        }
+        if ((j & 31) == 31 || j == nbaby) {
+            if (held) {
+                ok &= infra_insert_cas(tab, log2n, infra_key(kQ, kP), 0, kS);
+                ok &= infra_insert_cas(tab, log2n, infra_key(kQ, kPn), kMirror, kS);
+                held = false;
+            }
+            __syncwarp();
+        }
     }
-    if (!ok) {
+    if (!__all_sync(kFull, ok)) {
         done = 1;
         gres = -1;
         return;
@@ -74,42 +97,45 @@ __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n,
     Gg = (w.acc2 >> 1) % 3;
 }
 
+// reduce(X * Y): the textbook composition (compose = 0) or NUCOMP (1).
+__device__ __forceinline__ bool giant_mul(int compose, const Ideal &X, const Ideal &Y, int64_t d,
+                                          int64_t s, int64_t L, Ideal &out) {
+    return compose ? ideal_mul_nucomp(X, Y, d, s, L, out) : ideal_mul(X, Y, d, s, out);
+}
+
 // The BSGS of one d by one warp (all 32 lanes call it with the same d).
-__device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, uint32_t max_rounds) {
+__device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, uint32_t max_rounds,
+                              int compose) {
     const int lane = threadIdx.x & 31;
     GiantOut res{-1, 0, 0};
     for (uint32_t i = lane; i < (1u << log2n); i += 32) tab[i] = 0;
     __syncwarp();
-    // ---- baby steps (lane 0)
+    // ---- baby steps (all lanes)
     int done = 0, gres = 0, nb = 0;
     int64_t Ga = 0, Gb = 0;
     int Gg = 0;
-    if (lane == 0) {
-        if (d < kFastDLimit)
-            baby_phase<true>(d, tab, log2n, nbaby, done, gres, nb, Ga, Gb, Gg);
-        else
-            baby_phase<false>(d, tab, log2n, nbaby, done, gres, nb, Ga, Gb, Gg);
-    }
+    if (d < kFastDLimit)
+        baby_phase<true>(d, tab, log2n, nbaby, lane, done, gres, nb, Ga, Gb, Gg);
+    else
+        baby_phase<false>(d, tab, log2n, nbaby, lane, done, gres, nb, Ga, Gb, Gg);
     __syncwarp();
-    done = __shfl_sync(kFull, done, 0);
-    gres = __shfl_sync(kFull, gres, 0);
-    nb = __shfl_sync(kFull, nb, 0);
     res.baby = (uint32_t)nb;
     if (done) {
         res.g = gres;
         return res;
     }
     Ideal G;
-    G.a = __shfl_sync(kFull, Ga, 0);
-    G.b = __shfl_sync(kFull, Gb, 0);
-    G.g = __shfl_sync(kFull, Gg, 0);
+    G.a = Ga;
+    G.b = Gb;
+    G.g = Gg;
     const int64_t s = (int64_t)isqrt_u64(d);
     const int64_t dd = (int64_t)d;
+    const int64_t L = (int64_t)isqrt_u64((uint64_t)s);  // floor(d^(1/4))
     // ---- powers: P[i] = G^(2^i), i = 0..5 (the same on every lane)
     Ideal pw[6];
     pw[0] = G;
     bool ok = true;
-    for (int i = 1; i < 6; ++i) ok &= ideal_mul(pw[i - 1], pw[i - 1], dd, s, pw[i]);
+    for (int i = 1; i < 6; ++i) ok &= giant_mul(compose, pw[i - 1], pw[i - 1], dd, s, L, pw[i]);
     // lane t: mu = G^(t+2) by the bits of t+2 (2..33)
     Ideal mu;
     bool have = false;
@@ -121,7 +147,7 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
                 have = true;
             } else {
                 Ideal t;
-                ok &= ideal_mul(mu, pw[i], dd, s, t);
+                ok &= giant_mul(compose, mu, pw[i], dd, s, L, t);
                 mu = t;
             }
         }
@@ -144,7 +170,7 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
             return res;
         }
         Ideal t;
-        ok = ideal_mul(mu, stride, dd, s, t);
+        ok = giant_mul(compose, mu, stride, dd, s, L, t);
         mu = t;
         if (!__all_sync(kFull, ok)) return res;
         giants += 32;
@@ -173,7 +199,7 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
                                                uint8_t *__restrict__ glog,
                                                unsigned long long *__restrict__ acc,
                                                int *__restrict__ status, int nbaby, int log2n,
-                                               uint32_t max_rounds) {
+                                               uint32_t max_rounds, int compose) {
     extern __shared__ uint64_t smem_tab[];
     uint64_t *tab = smem_tab + (size_t)(threadIdx.x >> 5) * (1u << log2n);
     const int lane = threadIdx.x & 31;
@@ -190,7 +216,7 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
                 if (lane == 0) out_g[item] = 0;
                 continue;
             }
-            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds);
+            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds, compose);
             if (lane == 0) {
                 out_g[item] = (int8_t)(r.g >= 0 ? 1 + r.g : -1);
                 if (r.g < 0) atomicOr(status, kErrGiant);
@@ -200,7 +226,7 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
         } else {
             const uint32_t cand = cands[item];
             const uint64_t d = cand_to_d(segs, nseg, cand);
-            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds);
+            const GiantOut r = giant_one(d, tab, log2n, nbaby, max_rounds, compose);
             if (lane == 0) {
                 if (r.g < 0) {
                     atomicOr(status, kErrGiant);

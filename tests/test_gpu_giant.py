@@ -3,7 +3,10 @@
 The warp-per-d baby-step giant-step kernel answers single-d queries and,
 with a deferral threshold, takes over the long walks of a plan.  Every
 result is compared exactly with the oracle's full-period walk: the flag,
-and for the log output the class of eps_d in F_4*.
+and for the log output the class of eps_d in F_4*.  Each test runs with
+both giant-step compositions: the textbook product followed by rho steps,
+and NUCOMP/NUDUPL/NUCOMPchoose (Algorithms 2-4), whose class bookkeeping
+goes through gamma mod 2O_K -- a wrong class there changes log eps_d.
 """
 import concurrent.futures as cf
 
@@ -17,12 +20,21 @@ from test_oracle import paper
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[E.EIS_COMPOSE_TEXTBOOK, E.EIS_COMPOSE_NUCOMP],
+                ids=["textbook", "nucomp"])
+def ctx(request):
     E.build()
     c = E.Context(0)
+    c.set_option(E.EIS_OPT_GIANT_COMPOSE, request.param)
+    assert c.get_option(E.EIS_OPT_GIANT_COMPOSE) == request.param
     yield c
     c.close()
+
+
+def test_compose_option_values(ctx):
+    with pytest.raises(E.EisError) as ei:
+        ctx.set_option(E.EIS_OPT_GIANT_COMPOSE, 2)
+    assert ei.value.code == E.EIS_EINVAL
 
 
 def _random_D(orc, rng, lo, hi, k):
