@@ -157,9 +157,11 @@ __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
 }
 
 // One baby step j -> j+1.  Always advances the state and adds
-// 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2; returns true when the
+// 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2 -- unless kRaw, where
+// acc2 is left alone and the caller sums 2[P == 3 mod 4] (the bit
+// __float_as_int(Pm) & 2) and the 2 per step itself; returns true when the
 // new state is the centre of the period (Q_{j+1} = Q_j or P_{j+1} = P_j).
-template <bool kFast>
+template <bool kFast, bool kRaw = false>
 __device__ __forceinline__ bool walk_step(WalkState &w) {
     float qf, Pn;
     if (kFast) {
@@ -183,7 +185,7 @@ __device__ __forceinline__ bool walk_step(WalkState &w) {
     }
     const float dP = __fsub_rn(w.Pm, Pn);                     // P_j - P_{j+1}
     const float Qn = __fmaf_rn(qf, dP, w.Qp);                 // Q_{j+1}
-    w.acc2 += 2 + (__float_as_int(Pn) & 2);
+    if (!kRaw) w.acc2 += 2 + (__float_as_int(Pn) & 2);
     const bool centre = (Qn == w.Q) | (dP == 0.0f);
     w.Qp = w.Q;
     w.Q = Qn;
@@ -193,9 +195,11 @@ __device__ __forceinline__ bool walk_step(WalkState &w) {
 
 // log eps_d (mod 3, in 0..2) once walk_step has returned true.  The centre
 // is of odd type (l = 2j+1) iff the last two Q are equal, else of even type.
-__device__ __forceinline__ int walk_finish(const WalkState &w) {
+// raw_steps: the number of kRaw steps in acc2 (their 2 each is added here).
+__device__ __forceinline__ int walk_finish(const WalkState &w, uint32_t raw_steps = 0) {
     const int t = __float_as_int(w.Pm) & 2;
-    const int g = (w.Q == w.Qp) ? (w.acc2 - 1 - (t >> 1)) : (w.acc2 - 2 - t);
+    const int acc = w.acc2 + 2 * (int)(raw_steps % 3);
+    const int g = (w.Q == w.Qp) ? (acc - 1 - (t >> 1)) : (acc - 2 - t);
     return g % 3;
 }
 

@@ -77,6 +77,12 @@ __global__ void __launch_bounds__(256) k_walk_plain(uint64_t d_first, uint64_t c
     add_steps(steps_acc, steps);
 }
 
+// Steps per warp vote in the persistent walk.
+#ifndef EIS_WALK_GROUP
+#define EIS_WALK_GROUP 10
+#endif
+constexpr int kWalkGroup = EIS_WALK_GROUP;
+
 // K5.  The survivor queue surv[0, *n_surv) holds global candidate indices in
 // increasing order; lanes take them from the end (largest d first within the
 // Seg layout, which is sorted by d0) so that the cheapest walks run last.
@@ -132,25 +138,67 @@ __device__ __forceinline__ void walk_persistent_body(
             }
         }
         if (!__any_sync(kFull, active)) break;
-        // Walk until some lane reaches its centre (or the step limit).  Idle
-        // lanes hold NaN states whose centre test is false.
+        // Walk until some lane reaches its centre (or the step limit),
+        // kWalkGroup steps per warp vote: the intermediate states stay in
+        // registers and a lane whose centre came early in the group takes
+        // that state back (the steps past it are wasted, a few per d).  Idle
+        // lanes hold NaN states whose centre test is false.  acc2 runs in
+        // kRaw form: the 2 per step is added from `done` at the end.
         const uint32_t cap = (kDefer && active && may_defer) ? min(defer_after, step_limit) : step_limit;
         uint32_t room = active ? cap - min(done, cap) : 0xffffffffu;
         for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
-        uint32_t n = 0;
-        bool hit;
+        uint32_t n = 0, back = 0;
+        bool hit = false;
         for (;;) {
-            hit = walk_step<kFast>(w);
-            if (__any_sync(kFull, hit)) { n += 1; break; }
-            hit = walk_step<kFast>(w);
-            if (__any_sync(kFull, hit)) { n += 2; break; }
-            n += 2;
+            // The hot loop keeps two predicates (a centre at the group's first
+            // step, and at any step); the exit path finds each lane's first
+            // centre from the kept states, by bit equality (the values are
+            // finite and non-zero on a lane with a centre, where it agrees
+            // with the float test), and its acc2 by subtracting the bits of
+            // the steps after it.
+            WalkState ws[kWalkGroup];
+            int m[kWalkGroup];  // 2[P == 3 mod 4] of each new state
+            ws[0] = w;
+            const bool c0 = walk_step<kFast, true>(ws[0]);
+            m[0] = __float_as_int(ws[0].Pm) & 2;
+            bool any = c0;
+#pragma unroll
+            for (int i = 1; i < kWalkGroup; ++i) {
+                ws[i] = ws[i - 1];
+                any |= walk_step<kFast, true>(ws[i]);
+                m[i] = __float_as_int(ws[i].Pm) & 2;
+            }
+            n += kWalkGroup;
+            int sum = 0;
+#pragma unroll
+            for (int i = 0; i < kWalkGroup; ++i) sum += m[i];
+            const int acc = w.acc2 + sum;
+            w = ws[kWalkGroup - 1];
+            w.acc2 = acc;
+            if (__any_sync(kFull, any)) {
+                hit = any;
+                int post = 0;  // bits of the steps after step i
+#pragma unroll
+                for (int i = kWalkGroup - 1; i >= 0; --i) {
+                    const bool c = i ? (any &&
+                                        ((__float_as_int(ws[i].Q) == __float_as_int(ws[i - 1].Q)) |
+                                         (__float_as_int(ws[i].Pm) == __float_as_int(ws[i - 1].Pm))))
+                                     : c0;
+                    if (c) {  // the last one written is the first centre
+                        w = ws[i];
+                        w.acc2 = acc - post;
+                        back = (uint32_t)(kWalkGroup - 1 - i);
+                    }
+                    post += m[i];
+                }
+                break;
+            }
             if (n >= room) break;
         }
         if (active) {
-            done += n;
+            done += n - back;
             if (hit) {
-                record_result(flags, glog, cand, walk_finish(w));
+                record_result(flags, glog, cand, walk_finish(w, done));
                 my_steps += done;
                 active = false;
                 walk_park_idle(w);
@@ -175,7 +223,7 @@ __device__ __forceinline__ void walk_persistent_body(
     add_steps(steps_acc, my_steps);
 }
 
-__global__ void __launch_bounds__(256) k_walk_persistent(
+__global__ void __launch_bounds__(256, 4) k_walk_persistent(
     const Seg *__restrict__ segs, uint32_t nseg, const uint32_t *__restrict__ surv,
     const uint32_t *__restrict__ n_surv_ptr, uint32_t *__restrict__ next_ptr,
     uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
