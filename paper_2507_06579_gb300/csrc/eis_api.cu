@@ -199,7 +199,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                     nullptr, p->d_segs, nseg, p->d_defer, p->d_ctr + 2, p->defer_cap,
                     p->d_ctr + 3, c->d_primes, c->d_sqtab, c->nprimes, nullptr, p->d_flags, p->d_glog,
                     p->d_steps + 1, p->d_status, p->giant_nbaby, p->giant_log2n, kGiantMaxRounds,
-                    c->giant_compose);
+                    c->giant_compose, nullptr);
                 ++launches;
             }
             record(p->ev[4], s, capturing);
@@ -958,11 +958,17 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
     std::memset(&c->last, 0, sizeof(c->last));
     c->last.candidates = 1;
     int res = 0;  // 0: not in D, else 1 + log eps_d
+    // square-free test by the whole GPU (d_query[40], 0 = square-free)
+    unsigned char *q = c->d_query;  // [0] d, [8] out, [12] status, [16] acc[2], [32] next, [40] flag
+    uint32_t *sq_flag = reinterpret_cast<uint32_t *>(q + 40);
+    EIS_CK(cudaMemsetAsync(q, 0, 64, c->stream));
+    k_sqfree_one<<<c->sm_count * 2, 256, 0, c->stream>>>(d, c->d_sqtab, c->nprimes, sq_flag);
+    EIS_CK(cudaGetLastError());
     if (c->mode == EIS_MODE_PLAIN) {
         // one lane walks the half period
         EIS_CK(cudaMemsetAsync(c->d_single, 0, 4 * sizeof(int), c->stream));
         k_walk_single<<<1, 32, 0, c->stream>>>(d, c->d_primes, c->d_sqtab, c->nprimes, c->d_single,
-                                               c->d_single + 2, limit);
+                                               c->d_single + 2, limit, sq_flag);
         EIS_CK(cudaGetLastError());
         int h[4] = {0, 0, 0, 0};
         EIS_CK(cudaMemcpyAsync(h, c->d_single, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -975,15 +981,13 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
         int nbaby, log2n;
         giant_params(d, c->giant_stride, nbaby, log2n);
         log2n = std::min(log2n, kGiantMaxLog2);
-        unsigned char *q = c->d_query;  // [0] d, [8] out, [12] status, [16] acc[2], [32] next
-        EIS_CK(cudaMemsetAsync(q, 0, 64, c->stream));
         EIS_CK(cudaMemcpyAsync(q, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
         k_giant<<<1, 32, (size_t)8 << log2n, c->stream>>>(
             reinterpret_cast<const uint64_t *>(q), nullptr, 0, nullptr, nullptr, 1,
             reinterpret_cast<uint32_t *>(q + 32), c->d_primes, c->d_sqtab, c->nprimes,
             reinterpret_cast<int8_t *>(q + 8), nullptr, nullptr,
             reinterpret_cast<unsigned long long *>(q + 16), reinterpret_cast<int *>(q + 12), nbaby,
-            log2n, kGiantMaxRounds, c->giant_compose);
+            log2n, kGiantMaxRounds, c->giant_compose, sq_flag);
         EIS_CK(cudaGetLastError());
         unsigned char h[64];
         EIS_CK(cudaMemcpyAsync(h, q, 64, cudaMemcpyDeviceToHost, c->stream));

@@ -157,11 +157,9 @@ __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
 }
 
 // One baby step j -> j+1.  Always advances the state and adds
-// 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2 -- unless kRaw, where
-// acc2 is left alone and the caller sums 2[P == 3 mod 4] (the bit
-// __float_as_int(Pm) & 2) and the 2 per step itself; returns true when the
+// 2 log(P_{j+1}) = 2 + 2[P_{j+1} == 3 mod 4] to acc2; returns true when the
 // new state is the centre of the period (Q_{j+1} = Q_j or P_{j+1} = P_j).
-template <bool kFast, bool kRaw = false>
+template <bool kFast>
 __device__ __forceinline__ bool walk_step(WalkState &w) {
     float qf, Pn;
     if (kFast) {
@@ -185,7 +183,7 @@ __device__ __forceinline__ bool walk_step(WalkState &w) {
     }
     const float dP = __fsub_rn(w.Pm, Pn);                     // P_j - P_{j+1}
     const float Qn = __fmaf_rn(qf, dP, w.Qp);                 // Q_{j+1}
-    if (!kRaw) w.acc2 += 2 + (__float_as_int(Pn) & 2);
+    w.acc2 += 2 + (__float_as_int(Pn) & 2);
     const bool centre = (Qn == w.Q) | (dP == 0.0f);
     w.Qp = w.Q;
     w.Q = Qn;
@@ -195,11 +193,99 @@ __device__ __forceinline__ bool walk_step(WalkState &w) {
 
 // log eps_d (mod 3, in 0..2) once walk_step has returned true.  The centre
 // is of odd type (l = 2j+1) iff the last two Q are equal, else of even type.
-// raw_steps: the number of kRaw steps in acc2 (their 2 each is added here).
-__device__ __forceinline__ int walk_finish(const WalkState &w, uint32_t raw_steps = 0) {
+__device__ __forceinline__ int walk_finish(const WalkState &w) {
     const int t = __float_as_int(w.Pm) & 2;
-    const int acc = w.acc2 + 2 * (int)(raw_steps % 3);
-    const int g = (w.Q == w.Qp) ? (acc - 1 - (t >> 1)) : (acc - 2 - t);
+    const int g = (w.Q == w.Qp) ? (w.acc2 - 1 - (t >> 1)) : (w.acc2 - 2 - t);
+    return g % 3;
+}
+
+// ---------------------------------------------------------------- lean walk
+// The persistent walk's state.  P_j is carried only inside num = P_j + s
+// (+ 1/2 on the fast path): the next num is C - r with C = 2s (+1) and r the
+// remainder (+ 1/2), and num - num' = P_j - P_{j+1}.  The class bit
+// x_j = [P_j == 3 mod 4] follows from P_{j+1} = q_j Q_j - P_j with
+// Q_j == 2 (mod 4): x_{j+1} = 1 xor (q_j mod 2) xor x_j, where q_j mod 2 is
+// the low bit of the quotient in 2^23 + q form.  Six FMA-pipe instructions,
+// one MUFU.RCP, two compares and one LOP3 per step.
+struct LeanState {
+    float num;  // P_j + s (+ 1/2 when kFast)
+    float Q;    // Q_j
+    float Qp;   // Q_{j-1}
+    int x;      // [P_j == 3 mod 4]
+    int acc;    // 1 + x_1 + sum of x over the steps taken (the 1 per step apart)
+};
+
+// Idle lanes: NaN everywhere, so both centre tests compare false.
+__device__ __forceinline__ void lean_park_idle(LeanState &w, float &C) {
+    const float nan = __int_as_float(0x7fffffff);
+    w.num = nan;
+    w.Q = nan;
+    w.Qp = nan;
+    w.x = 0;
+    w.acc = 0;
+    C = nan;
+}
+
+// First step from (P_0, Q_0) = (1, 2) in 64-bit integers, as walk_init.
+// Returns true when the period is 1, with *g = log eps_d.
+template <bool kFast>
+__device__ __forceinline__ bool lean_init(uint64_t d, LeanState &w, float &C, int &g) {
+    const uint64_t s = isqrt_u64(d);
+    const uint64_t a0 = (1 + s) >> 1;
+    const uint64_t P1 = 2 * a0 - 1;
+    const uint64_t Q1 = (d - P1 * P1) >> 1;
+    const int x1 = (int)((P1 >> 1) & 1);
+    if (Q1 == 2) {
+        g = 1 + x1;
+        return true;
+    }
+    const uint32_t s2 = 2 * (uint32_t)s;
+    w.num = kFast ? __fadd_rn(__uint2float_rn((uint32_t)(P1 + s)), 0.5f)
+                  : __uint2float_rn((uint32_t)(P1 + s));
+    w.Q = __uint2float_rn((uint32_t)Q1);
+    w.Qp = 2.0f;
+    w.x = x1;
+    w.acc = 1 + x1;
+    C = __uint2float_rn(kFast ? s2 + 1 : s2);
+    return false;
+}
+
+// One step j -> j+1 (acc is left to the caller).  Returns true when the new
+// state is the centre of the period (Q_{j+1} = Q_j or P_{j+1} = P_j).
+template <bool kFast>
+__device__ __forceinline__ bool lean_step(LeanState &w, float C) {
+    const float rq = rcp_approx(w.Q);
+    float qm, qf, r;
+    if (kFast) {
+        qm = __fmaf_rd(w.num, rq, kMagic);        // 2^23 + q exactly
+        qf = __fsub_rn(qm, kMagic);
+        r = __fmaf_rn(-qf, w.Q, w.num);           // remainder + 1/2
+    } else {
+        qm = __fmaf_rd(w.num, rq, kMagic - 0.5f); // 2^23 + (q or q-1)
+        qf = __fsub_rn(qm, kMagic);
+        r = __fmaf_rn(-qf, w.Q, w.num);           // remainder, in [0, 2Q)
+        if (r >= w.Q) {
+            r = __fsub_rn(r, w.Q);
+            qf = __fadd_rn(qf, 1.0f);
+            qm = __fadd_rn(qm, 1.0f);
+        }
+    }
+    const float numn = __fsub_rn(C, r);           // P_{j+1} + s (+ 1/2)
+    const float dP = __fsub_rn(w.num, numn);      // P_j - P_{j+1}
+    const float Qn = __fmaf_rn(qf, dP, w.Qp);     // Q_{j+1}
+    w.x = ~(w.x ^ __float_as_int(qm)) & 1;
+    const bool centre = (Qn == w.Q) | (dP == 0.0f);
+    w.Qp = w.Q;
+    w.Q = Qn;
+    w.num = numn;
+    return centre;
+}
+
+// log eps_d (mod 3) at a centre reached after `steps` steps from state 1:
+// S_j = acc + steps, and the odd / even centre rules of walk_finish.
+__device__ __forceinline__ int lean_finish(const LeanState &w, uint32_t steps) {
+    const int S = w.acc + (int)(steps % 3);
+    const int g = (w.Q == w.Qp) ? (2 * S - 1 - w.x) : (2 * S - 2 - 2 * w.x);
     return g % 3;
 }
 

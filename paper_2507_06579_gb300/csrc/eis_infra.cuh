@@ -15,10 +15,12 @@
 // floor((P + s + 1)/Q) for Q < 0 (s = floor(sqrt d)), P' = qQ - P,
 // Q' = (d - P'^2)/Q, and the class gains log((P'-1)/2 + omega) mod 2, which
 // is 1 when P' == 1 (mod 4) and 2 when P' == 3 (mod 4) (Q/2 odd, sign +-1
-// == 1 mod 2).  P'^2 can exceed 2^64 on the first steps, but |Q'| < 2^62, so
-// Q' is recovered exactly from d - P'^2 mod 2^64 by exact division: with
-// Q = 2a, ((d - P'^2) mod 2^64) >> 1 = a Q' (mod 2^63), times the inverse of
-// a modulo 2^64 (Newton iteration x <- x(2 - a x)).
+// == 1 mod 2).  Q_{-1} = (d - P^2)/Q is found once, by exact division: P^2
+// can exceed 2^64, but the quotient is below 2^62, so with Q = 2a,
+// ((d - P^2) mod 2^64) >> 1 = a Q_{-1} (mod 2^63), times the inverse of a
+// modulo 2^64 (Newton iteration x <- x(2 - a x)).  Every step after that
+// uses Q' = Q_{-1} + q (P - P') (from Q_{-1} Q = d - P^2 and P + P' = qQ),
+// with no division; q(P - P') = Q' - Q_{-1} stays below 2^47.
 //
 // Reduced: Q > 0, 0 < P <= s and s - P < Q <= s + P (sqrt d irrational).
 #pragma once
@@ -94,6 +96,24 @@ __device__ __forceinline__ int64_t floor_div(int64_t x, int64_t y) {
     return q;
 }
 
+// floor(x / y) for |x|, |y| < 2^47, y != 0.  The fp32 estimate
+// x * rcp(y) has relative error below 2^-21.4 (two conversions, rcp.approx
+// and the product), so while it is below 2^20 in magnitude it lies within
+// 0.4 of x/y and its floor is q - 1, q or q + 1; one integer correction each
+// way fixes it.  Larger quotients take the 64-bit division.
+__device__ __forceinline__ int64_t floor_div_fast(int64_t x, int64_t y) {
+    const float e = floorf(__fmul_rn((float)x, rcp_approx((float)y)));
+    if (fabsf(e) >= 1048576.0f) return floor_div(x, y);
+    int64_t q = (int64_t)(int32_t)e;
+    const int64_t r = x - q * y;  // floor wants 0 <= r < y (y > 0), y < r <= 0 (y < 0)
+    if (y > 0) {
+        if (r < 0) --q; else if (r >= y) ++q;
+    } else {
+        if (r > 0) --q; else if (r <= y) ++q;
+    }
+    return q;
+}
+
 // Inverse of an odd a modulo 2^64.
 __device__ __forceinline__ uint64_t inv_odd_u64(uint64_t a) {
     uint64_t x = a;  // a * a == 1 (mod 8): 3 correct bits
@@ -148,20 +168,31 @@ __device__ __forceinline__ bool ideal_is_reduced(int64_t P, int64_t Q, int64_t s
     return Q > 0 && P > 0 && P <= s && s - P < Q && Q <= s + P;
 }
 
-// rho until reduced; returns the class gained, or -1 past max_steps.
+// (d - P^2) / Q exactly, for Q == 2 (mod 4) dividing d - P^2 and a quotient
+// below 2^62 in magnitude.
+__device__ __forceinline__ int64_t exact_quot(int64_t d, int64_t P, int64_t Q) {
+    const uint64_t X = (uint64_t)d - (uint64_t)P * (uint64_t)P;  // d - P^2 mod 2^64
+    const int64_t ha = Q > 0 ? Q / 2 : -(Q / 2);                   // |Q|/2, odd
+    const uint64_t m = ((X >> 1) * inv_odd_u64((uint64_t)ha)) & 0x7fffffffffffffffull;
+    const int64_t v = (m & 0x4000000000000000ull) ? (int64_t)(m | 0x8000000000000000ull) : (int64_t)m;
+    return Q < 0 ? -v : v;
+}
+
+// rho until reduced; returns the class gained, or -1 past max_steps.  P must
+// lie within about |Q| + 2^23 of 0 on entry (true of every composition here),
+// which keeps Q_{-1} and every later value below 2^47.
 __device__ __forceinline__ int ideal_reduce(int64_t &P, int64_t &Q, int64_t d, int64_t s,
                                             int max_steps) {
+    if (ideal_is_reduced(P, Q, s)) return 0;
     int g = 0;
+    int64_t Qm = exact_quot(d, P, Q);  // Q_{-1}
     for (int it = 0; !ideal_is_reduced(P, Q, s); ++it) {
         if (it >= max_steps) return -1;
-        const int64_t q = Q > 0 ? floor_div(P + s, Q) : floor_div(P + s + 1, Q);
+        const int64_t q = Q > 0 ? floor_div_fast(P + s, Q) : floor_div_fast(P + s + 1, Q);
         const int64_t Pn = q * Q - P;
-        const uint64_t X = (uint64_t)d - (uint64_t)Pn * (uint64_t)Pn;  // d - P'^2 mod 2^64
-        const int64_t ha = Q > 0 ? Q / 2 : -(Q / 2);                    // |Q|/2, odd
-        const uint64_t m = ((X >> 1) * inv_odd_u64((uint64_t)ha)) & 0x7fffffffffffffffull;
-        int64_t Qn = (m & 0x4000000000000000ull) ? (int64_t)(m | 0x8000000000000000ull) : (int64_t)m;
-        if (Q < 0) Qn = -Qn;
+        const int64_t Qn = Qm + q * (P - Pn);
         g += 1 + (int)((Pn >> 1) & 1);
+        Qm = Q;
         P = Pn;
         Q = Qn;
     }

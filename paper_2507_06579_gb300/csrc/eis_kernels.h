@@ -33,8 +33,10 @@ __global__ void k_giant(const uint64_t *ds, const Seg *segs, uint32_t nseg, cons
                         const uint32_t *primes, const uint64_t *sqtab, uint32_t nprimes,
                         int8_t *out_g, uint32_t *flags,
                         uint8_t *glog, unsigned long long *acc, int *status, int nbaby, int log2n,
-                        uint32_t max_rounds, int compose);
+                        uint32_t max_rounds, int compose, const uint32_t *sq_flag);
 __global__ void k_walk_single(uint64_t d, const uint32_t *primes, const uint64_t *sqtab,
-                              uint32_t nprimes, int *out, int *status, uint32_t step_limit);
+                              uint32_t nprimes, int *out, int *status, uint32_t step_limit,
+                              const uint32_t *sq_flag);
+__global__ void k_sqfree_one(uint64_t d, const uint64_t *sqtab, uint32_t nprimes, uint32_t *flag);
 
 }  // namespace eis

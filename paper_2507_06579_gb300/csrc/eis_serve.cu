@@ -205,7 +205,7 @@ bool launch_batch(eis_server *s, Slot &sl) {
             k_giant<<<s->giant_grid, 32, (size_t)8 << log2n, st>>>(
                 nullptr, sl.d_segs, nseg, sl.d_defer, sl.d_ctr + 2, s->defer_cap, sl.d_ctr + 3,
                 cv.d_primes, cv.d_sqtab, cv.nprimes, nullptr, sl.d_flags, nullptr, sl.d_steps + 1,
-                sl.d_status, nbaby, log2n, 1u << 20, cv.giant_compose);
+                sl.d_status, nbaby, log2n, 1u << 20, cv.giant_compose, nullptr);
         }
         k_count<<<nt, 256, 0, st>>>(sl.d_tiles, sl.d_flags, sl.d_sqfree, sl.d_counts, nullptr,
                                     nullptr);
@@ -226,7 +226,8 @@ bool launch_batch(eis_server *s, Slot &sl) {
             reinterpret_cast<uint32_t *>(sl.d_mem_ctl), cv.d_primes, cv.d_sqtab, cv.nprimes,
             sl.d_mem_out,
             nullptr, nullptr, reinterpret_cast<unsigned long long *>(sl.d_mem_ctl + 8),
-            reinterpret_cast<int *>(sl.d_mem_ctl + 24), nbaby, log2n, 1u << 20, cv.giant_compose);
+            reinterpret_cast<int *>(sl.d_mem_ctl + 24), nbaby, log2n, 1u << 20, cv.giant_compose,
+            nullptr);
         cudaMemcpyAsync(sl.h_mem_out, sl.d_mem_out, nmem, cudaMemcpyDeviceToHost, st);
     }
     cudaMemcpyAsync(sl.h_counts, sl.d_counts, 2 * nseg * sizeof(unsigned long long),

@@ -57,13 +57,53 @@ __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n,
         const int64_t P1 = __float_as_int(w.Pm) & 0x7fffff;
         ok = infra_insert_cas(tab, log2n, infra_key(2, P1), 0, 0);
     }
-    int64_t kQ = 0, kP = 0, kPn = 0;  // the state this lane holds
-    int kS = 0;
-    bool held = false;
-    for (int j = 1; j <= nbaby; ++j) {
-        const int64_t Pj = __float_as_int(w.Pm) & 0x7fffff;
-        const int64_t Qj = (int64_t)w.Q;
-        const int Sj = (w.acc2 >> 1) % 3;
+    // The state this lane holds, as the walk's raw registers (the integer
+    // keys are formed at insert time).
+    float kQ = 0.0f, kPm = 0.0f, kPn = 0.0f;
+    int kAcc = 0;
+    int j = 1;  // the next state to step from
+    // Whole batches of 32 steps, unrolled with no branch inside: lane t holds
+    // state j + t.  A centre anywhere in the batch sends the warp back to the
+    // batch's first state to find it step by step (once per d at most).
+    for (; j + 31 <= nbaby; j += 32) {
+        const WalkState w0 = w;
+        bool cen = false;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const bool mine = lane == t;
+            kQ = mine ? w.Q : kQ;
+            kPm = mine ? w.Pm : kPm;
+            kAcc = mine ? w.acc2 : kAcc;
+            cen |= walk_step<kFast>(w);
+            kPn = mine ? w.Pm : kPn;
+        }
+        if (cen) {
+            w = w0;
+            for (int t = 0; t < 32; ++t) {
+                ++nb;
+                if (walk_step<kFast>(w)) break;
+            }
+            done = 1;
+            gres = walk_finish(w);
+            return;
+        }
+        nb += 32;
+        const int64_t Qj = (int64_t)kQ;
+        const int64_t Pj = __float_as_int(kPm) & 0x7fffff;
+        const int64_t Pn = __float_as_int(kPn) & 0x7fffff;
+        const int Sj = (kAcc >> 1) % 3;
+        ok &= infra_insert_cas(tab, log2n, infra_key(Qj, Pj), 0, Sj);
+        ok &= infra_insert_cas(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
+        __syncwarp();
+    }
+    // The rest (N not a multiple of 32), one step at a time: lane t holds
+    // state j0 + t of this last batch.
+    const int j0 = j;
+    for (; j <= nbaby; ++j) {
+        const bool mine = (j - j0) == lane;
+        kQ = mine ? w.Q : kQ;
+        kPm = mine ? w.Pm : kPm;
+        kAcc = mine ? w.acc2 : kAcc;
         const bool centre = walk_step<kFast>(w);
         ++nb;
         if (centre) {
@@ -71,22 +111,17 @@ __device__ __forceinline__ void baby_phase(uint64_t d, uint64_t *tab, int log2n,
             gres = walk_finish(w);
             return;
         }
-        if ((j & 31) == lane) {
-            kQ = Qj;
-            kP = Pj;
-            kPn = __float_as_int(w.Pm) & 0x7fffff;
-            kS = Sj;
-            held = true;
-        }
-        if ((j & 31) == 31 || j == nbaby) {
-            if (held) {
-                ok &= infra_insert_cas(tab, log2n, infra_key(kQ, kP), 0, kS);
-                ok &= infra_insert_cas(tab, log2n, infra_key(kQ, kPn), kMirror, kS);
-                held = false;
-            }
-            __syncwarp();
-        }
+        kPn = mine ? w.Pm : kPn;
     }
+    if (lane < j - j0) {
+        const int64_t Qj = (int64_t)kQ;
+        const int64_t Pj = __float_as_int(kPm) & 0x7fffff;
+        const int64_t Pn = __float_as_int(kPn) & 0x7fffff;
+        const int Sj = (kAcc >> 1) % 3;
+        ok &= infra_insert_cas(tab, log2n, infra_key(Qj, Pj), 0, Sj);
+        ok &= infra_insert_cas(tab, log2n, infra_key(Qj, Pn), kMirror, Sj);
+    }
+    __syncwarp();
     if (!__all_sync(kFull, ok)) {
         done = 1;
         gres = -1;
@@ -131,29 +166,33 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
     const int64_t s = (int64_t)isqrt_u64(d);
     const int64_t dd = (int64_t)d;
     const int64_t L = (int64_t)isqrt_u64((uint64_t)s);  // floor(d^(1/4))
-    // ---- powers: P[i] = G^(2^i), i = 0..5 (the same on every lane)
-    Ideal pw[6];
-    pw[0] = G;
+    // ---- lane t: mu = G^(t+1) by a product scan over the lanes (five rounds
+    // of shuffles, each a composition on the lanes that receive), the stride
+    // G^32 from lane 31, then mu = G^(t+2): six compositions deep.
+    Ideal mu = G;
     bool ok = true;
-    for (int i = 1; i < 6; ++i) ok &= giant_mul(compose, pw[i - 1], pw[i - 1], dd, s, L, pw[i]);
-    // lane t: mu = G^(t+2) by the bits of t+2 (2..33)
-    Ideal mu;
-    bool have = false;
-    const int k = lane + 2;
-    for (int i = 0; i < 6; ++i) {
-        if ((k >> i) & 1) {
-            if (!have) {
-                mu = pw[i];
-                have = true;
-            } else {
-                Ideal t;
-                ok &= giant_mul(compose, mu, pw[i], dd, s, L, t);
-                mu = t;
-            }
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        Ideal o;
+        o.a = __shfl_up_sync(kFull, mu.a, k);
+        o.b = __shfl_up_sync(kFull, mu.b, k);
+        o.g = __shfl_up_sync(kFull, mu.g, k);
+        if (lane >= k) {
+            Ideal t;
+            ok &= giant_mul(compose, mu, o, dd, s, L, t);
+            mu = t;
         }
     }
-    const Ideal stride = pw[5];  // G^32
-    uint32_t giants = 15;        // compositions spent on the powers (upper bound)
+    Ideal stride;  // G^32
+    stride.a = __shfl_sync(kFull, mu.a, 31);
+    stride.b = __shfl_sync(kFull, mu.b, 31);
+    stride.g = __shfl_sync(kFull, mu.g, 31);
+    {
+        Ideal t;
+        ok &= giant_mul(compose, mu, G, dd, s, L, t);
+        mu = t;
+    }
+    uint32_t giants = 6;  // compositions on a lane's way to its first giant step
     if (!__all_sync(kFull, ok)) return res;
     for (uint32_t r = 0; r < max_rounds; ++r) {
         const uint64_t e = infra_find(tab, log2n, infra_key(2 * mu.a, mu.b));
@@ -183,7 +222,8 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
 // One warp per item; items are taken from a global counter.
 //   ds != nullptr : item i is d = ds[i]; out_g[i] = 0 (not in D),
 //                   1 + log eps_d, or -1 (error); the square-free test runs
-//                   against the prime table (division-free, eis_common.cuh).
+//                   against the prime table (division-free, eis_common.cuh),
+//                   unless sq_flag (one d) holds the answer of k_sqfree_one.
 //   ds == nullptr : item i is candidate cands[i] of the Seg layout (already
 //                   square-free); its flag bit / log byte are written.
 // Dynamic shared memory: (blockDim.x / 32) tables of 2^log2n uint64.
@@ -199,7 +239,8 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
                                                uint8_t *__restrict__ glog,
                                                unsigned long long *__restrict__ acc,
                                                int *__restrict__ status, int nbaby, int log2n,
-                                               uint32_t max_rounds, int compose) {
+                                               uint32_t max_rounds, int compose,
+                                               const uint32_t *__restrict__ sq_flag) {
     extern __shared__ uint64_t smem_tab[];
     uint64_t *tab = smem_tab + (size_t)(threadIdx.x >> 5) * (1u << log2n);
     const int lane = threadIdx.x & 31;
@@ -212,7 +253,9 @@ __global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
         if (item >= n) break;
         if (ds) {
             const uint64_t d = ds[item];
-            if (d % 8 != 5 || !warp_squarefree_fast(d, primes, sqtab, nprimes)) {
+            const bool sq = sq_flag ? (*sq_flag == 0)
+                                    : warp_squarefree_fast(d, primes, sqtab, nprimes);
+            if (d % 8 != 5 || !sq) {
                 if (lane == 0) out_g[item] = 0;
                 continue;
             }

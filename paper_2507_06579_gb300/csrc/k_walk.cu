@@ -102,8 +102,9 @@ __device__ __forceinline__ void walk_persistent_body(
     // A walk longer than defer_after steps is handed to the giant-step kernel
     // (while the defer list has room).
     bool may_defer = kDefer;
-    WalkState w;
-    walk_park_idle(w);
+    LeanState w;
+    float C;  // 2s (+1): num' = C - remainder
+    lean_park_idle(w, C);
     bool active = false;
     bool exhausted = false;  // warp-uniform
     uint32_t cand = 0;
@@ -126,9 +127,9 @@ __device__ __forceinline__ void walk_persistent_body(
                     const uint64_t d = cand_to_d(segs, nseg, cand);
                     int g;
                     my_steps += 1;
-                    if (walk_init<kFast>(d, w, g)) {
+                    if (lean_init<kFast>(d, w, C, g)) {
                         record_result(flags, glog, cand, g);
-                        walk_park_idle(w);
+                        lean_park_idle(w, C);
                     } else {
                         active = true;
                         done = 0;
@@ -142,8 +143,7 @@ __device__ __forceinline__ void walk_persistent_body(
         // kWalkGroup steps per warp vote: the intermediate states stay in
         // registers and a lane whose centre came early in the group takes
         // that state back (the steps past it are wasted, a few per d).  Idle
-        // lanes hold NaN states whose centre test is false.  acc2 runs in
-        // kRaw form: the 2 per step is added from `done` at the end.
+        // lanes hold NaN states whose centre test is false.
         const uint32_t cap = (kDefer && active && may_defer) ? min(defer_after, step_limit) : step_limit;
         uint32_t room = active ? cap - min(done, cap) : 0xffffffffu;
         for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
@@ -154,42 +154,39 @@ __device__ __forceinline__ void walk_persistent_body(
             // step, and at any step); the exit path finds each lane's first
             // centre from the kept states, by bit equality (the values are
             // finite and non-zero on a lane with a centre, where it agrees
-            // with the float test), and its acc2 by subtracting the bits of
-            // the steps after it.
-            WalkState ws[kWalkGroup];
-            int m[kWalkGroup];  // 2[P == 3 mod 4] of each new state
+            // with the float test), and its acc by subtracting the class
+            // bits of the steps after it.
+            LeanState ws[kWalkGroup];
             ws[0] = w;
-            const bool c0 = walk_step<kFast, true>(ws[0]);
-            m[0] = __float_as_int(ws[0].Pm) & 2;
+            const bool c0 = lean_step<kFast>(ws[0], C);
             bool any = c0;
 #pragma unroll
             for (int i = 1; i < kWalkGroup; ++i) {
                 ws[i] = ws[i - 1];
-                any |= walk_step<kFast, true>(ws[i]);
-                m[i] = __float_as_int(ws[i].Pm) & 2;
+                any |= lean_step<kFast>(ws[i], C);
             }
             n += kWalkGroup;
             int sum = 0;
 #pragma unroll
-            for (int i = 0; i < kWalkGroup; ++i) sum += m[i];
-            const int acc = w.acc2 + sum;
+            for (int i = 0; i < kWalkGroup; ++i) sum += ws[i].x;
+            const int acc = w.acc + sum;
             w = ws[kWalkGroup - 1];
-            w.acc2 = acc;
+            w.acc = acc;
             if (__any_sync(kFull, any)) {
                 hit = any;
-                int post = 0;  // bits of the steps after step i
+                int post = 0;  // class bits of the steps after step i
 #pragma unroll
                 for (int i = kWalkGroup - 1; i >= 0; --i) {
                     const bool c = i ? (any &&
                                         ((__float_as_int(ws[i].Q) == __float_as_int(ws[i - 1].Q)) |
-                                         (__float_as_int(ws[i].Pm) == __float_as_int(ws[i - 1].Pm))))
+                                         (__float_as_int(ws[i].num) == __float_as_int(ws[i - 1].num))))
                                      : c0;
                     if (c) {  // the last one written is the first centre
                         w = ws[i];
-                        w.acc2 = acc - post;
+                        w.acc = acc - post;
                         back = (uint32_t)(kWalkGroup - 1 - i);
                     }
-                    post += m[i];
+                    post += ws[i].x;
                 }
                 break;
             }
@@ -198,17 +195,17 @@ __device__ __forceinline__ void walk_persistent_body(
         if (active) {
             done += n - back;
             if (hit) {
-                record_result(flags, glog, cand, walk_finish(w, done));
+                record_result(flags, glog, cand, lean_finish(w, done));
                 my_steps += done;
                 active = false;
-                walk_park_idle(w);
+                lean_park_idle(w, C);
             } else if (kDefer && may_defer && done >= defer_after && done < step_limit) {
                 const uint32_t slot = atomicAdd(defer_count, 1u);
                 if (slot < defer_cap) {
                     defer_list[slot] = cand;
                     my_steps += done;
                     active = false;
-                    walk_park_idle(w);
+                    lean_park_idle(w, C);
                 } else {
                     may_defer = false;  // list full: this walk goes on here
                 }
@@ -216,7 +213,7 @@ __device__ __forceinline__ void walk_persistent_body(
                 atomicOr(status, kErrSteps);
                 my_steps += done;
                 active = false;
-                walk_park_idle(w);
+                lean_park_idle(w, C);
             }
         }
     }
@@ -242,14 +239,29 @@ __global__ void __launch_bounds__(256, 4) k_walk_persistent(
 #undef EIS_WALK_BODY
 }
 
+// Square-free test of one d by a whole grid: *flag |= 1 when p^2 | d for an
+// odd prime p of the table.  A prime with p^2 > d cannot divide d (d > 0)
+// and the divisibility test is exact for any d, so the whole table is
+// scanned with no bound (d < 2^44 needs p < 2^22, the table's range).
+__global__ void __launch_bounds__(256) k_sqfree_one(uint64_t d, const uint64_t *__restrict__ sqtab,
+                                                    uint32_t nprimes, uint32_t *__restrict__ flag) {
+    bool hit = false;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nprimes;
+         i += gridDim.x * blockDim.x)
+        hit |= d * sqtab[2 * i] <= sqtab[2 * i + 1];
+    if (__any_sync(kFull, hit) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 // Membership query for one d (one warp).  out[0] = 0 (d not in D) or
 // 1 + log eps_d; out[1] = steps.  The square-free test covers every odd prime
-// p with p^2 <= d from the table (d < 2^44 needs p < 2^22).
+// p with p^2 <= d from the table (d < 2^44 needs p < 2^22), or is read from
+// sq_flag (k_sqfree_one) when given.
 __global__ void __launch_bounds__(32) k_walk_single(uint64_t d, const uint32_t *__restrict__ primes,
                                                     const uint64_t *__restrict__ sqtab,
                                                     uint32_t nprimes, int *__restrict__ out,
-                                                    int *__restrict__ status, uint32_t step_limit) {
-    const bool sq = warp_squarefree_fast(d, primes, sqtab, nprimes);
+                                                    int *__restrict__ status, uint32_t step_limit,
+                                                    const uint32_t *__restrict__ sq_flag) {
+    const bool sq = sq_flag ? (*sq_flag == 0) : warp_squarefree_fast(d, primes, sqtab, nprimes);
     if (threadIdx.x != 0) return;
     if (!sq || d % 8 != 5) {
         out[0] = 0;
