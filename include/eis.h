@@ -188,7 +188,8 @@ typedef struct {
 /* Time candidate settings (CTAs per SM of the persistent walk, deferral of
  * long walks to the warp-per-d giant-step kernel and its threshold, the
  * giant-step baby count) on the sample [lo, hi) -- a window of the d-range
- * the context will serve -- and keep the fastest in the context.  Every
+ * the context will serve -- and keep the fastest in the context, provided it
+ * beats the previous setting by more than 2% (else the previous stays).  Every
  * candidate runs a full plan (sieve, walks, count); results are identical
  * for every setting, only time differs.  Takes a few passes of the sample. */
 int eis_autotune(eis_ctx *ctx, uint64_t lo, uint64_t hi, eis_tune_result *out);

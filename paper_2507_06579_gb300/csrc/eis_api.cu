@@ -156,6 +156,7 @@ static void giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n) {
 
 static constexpr int kGiantMaxLog2 = 14;  // 128 KB table per warp at most
 static constexpr uint32_t kGiantMaxRounds = 1u << 20;
+static constexpr double kTuneMargin = 0.98;  // autotuner: keep the current setting unless 2% faster
 
 static void record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
     if (capturing)
@@ -840,7 +841,10 @@ int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
             break;
         }
         ++trials;
-        if (ms < ms_best) {
+        // A setting replaces the current one only when it is faster by more
+        // than the sample's run-to-run noise (2%); the sample below the
+        // window is not the window itself.
+        if (ms < ms_best && ms < kTuneMargin * ms_prev) {
             ms_best = ms;
             best = st;
         }
