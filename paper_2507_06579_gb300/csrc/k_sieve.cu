@@ -172,37 +172,36 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict_
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Survivor queue: the global indices of the square-free candidates, tile by
-// tile in increasing order.  8 bitmap words per thread (256 threads = 2048
-// words = one tile).
+// K1b: the square-free candidates of each tile, in increasing order, as
+// a compact queue from tile_off[tile].  The tile is taken in chunks of 256
+// bitmap words, one per thread and read coalesced.  A block scan of the
+// words' popcounts places each word's survivors in a shared-memory stage,
+// and the block copies the stage to the queue with consecutive threads
+// writing consecutive entries, so the queue is written in whole lines.
 __global__ void __launch_bounds__(256) k_compact(const Tile *__restrict__ tiles,
                                                  const uint32_t *__restrict__ sqfree,
                                                  const uint32_t *__restrict__ tile_off,
                                                  uint32_t *__restrict__ surv) {
     __shared__ uint32_t red[32];
+    __shared__ uint32_t stage[256 * 32];  // one chunk: at most 8192 survivors
     const Tile t = tiles[blockIdx.x];
     const uint32_t nw = (t.ncand + 31) >> 5;
     const uint64_t wbase = t.cand0 >> 5;
-    constexpr uint32_t kPer = kTileWords / 256;
-    uint32_t v[kPer];
-    uint32_t cnt = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        const uint32_t w = threadIdx.x * kPer + k;
-        v[k] = (w < nw) ? sqfree[wbase + w] : 0u;
-        cnt += __popc(v[k]);
-    }
-    uint32_t tot;
-    uint32_t out = tile_off[blockIdx.x] + block_excl_scan(cnt, red, &tot);
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        uint32_t x = v[k];
-        const uint32_t cbase = (uint32_t)(t.cand0 + 32u * (threadIdx.x * kPer + k));
+    uint32_t out = tile_off[blockIdx.x];
+    for (uint32_t c0 = 0; c0 < nw; c0 += 256) {
+        const uint32_t w = c0 + threadIdx.x;
+        uint32_t x = (w < nw) ? sqfree[wbase + w] : 0u;
+        uint32_t tot;
+        uint32_t o = block_excl_scan((uint32_t)__popc(x), red, &tot);
+        const uint32_t cbase = (uint32_t)(t.cand0 + 32u * w);
         while (x) {
-            const int b = __ffs(x) - 1;
-            surv[out++] = cbase + (uint32_t)b;
+            stage[o++] = cbase + (uint32_t)(__ffs(x) - 1);
             x &= x - 1;
         }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tot; i += 256) surv[out + i] = stage[i];
+        out += tot;
+        __syncthreads();
     }
 }
 
