@@ -25,21 +25,43 @@ __device__ __forceinline__ void add_steps(unsigned long long *acc, unsigned long
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
 }
 
-// One whole half-period walk by one thread: false past step_limit steps;
-// otherwise g = log eps_d and n = steps after the first.
+// Steps per centre test in walk_one.
+constexpr int kOneGroup = 8;
+
+// One whole half-period walk by one thread, with the persistent walk's lean
+// step: false past step_limit steps; otherwise g = log eps_d and n = steps
+// after the first.  The centre is tested once per kOneGroup steps; a group
+// that contains it is walked again from its first state, one step at a time.
 template <bool kFast>
 __device__ __forceinline__ bool walk_one(uint64_t d, uint32_t step_limit, int &g, uint32_t &n) {
-    WalkState w;
+    LeanState w;
+    float C;
     n = 0;
-    if (walk_init<kFast>(d, w, g)) return true;
+    if (lean_init<kFast>(d, w, C, g)) return true;
     for (;;) {
-        if (walk_step<kFast>(w)) { n += 1; break; }
-        if (walk_step<kFast>(w)) { n += 2; break; }
-        n += 2;
+        const LeanState w0 = w;
+        bool any = false;
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < kOneGroup; ++i) {
+            any |= lean_step<kFast>(w, C);
+            sum += w.x;
+        }
+        if (any) {
+            w = w0;
+            for (int i = 0; i < kOneGroup; ++i) {
+                const bool c = lean_step<kFast>(w, C);
+                w.acc += w.x;
+                ++n;
+                if (c) break;
+            }
+            g = lean_finish(w, n);
+            return true;
+        }
+        w.acc += sum;
+        n += kOneGroup;
         if (n >= step_limit) return false;
     }
-    g = walk_finish(w);
-    return true;
 }
 
 // K2.  Candidates [cand_first, cand_first + ncand) of one Seg, d of the first
