@@ -58,10 +58,17 @@ __device__ __forceinline__ int64_t egcd32(int32_t a, int32_t b, int64_t &x, int6
     return a;
 }
 
-// Extended Euclid: returns gcd(a, b) >= 0 with x a + y b = gcd.
+// Extended Euclid: returns gcd(a, b) >= 0 with x a + y b = gcd.  Operands
+// below 2^31 in magnitude take the 32-bit loop on |a|, |b| (the cofactors'
+// signs follow the operands'); the forms' middle coefficients are negative.
 __device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t &x, int64_t &y) {
-    if (a >= 0 && b >= 0 && a < 0x7fffffff && b < 0x7fffffff)
-        return egcd32((int32_t)a, (int32_t)b, x, y);
+    const int64_t aa = a < 0 ? -a : a, ab = b < 0 ? -b : b;
+    if (aa < 0x7fffffff && ab < 0x7fffffff) {
+        const int64_t g = egcd32((int32_t)aa, (int32_t)ab, x, y);
+        if (a < 0) x = -x;
+        if (b < 0) y = -y;
+        return g;
+    }
     int64_t x0 = 1, y0 = 0, x1 = 0, y1 = 1;
     while (b != 0) {
         const int64_t q = a / b;
@@ -241,12 +248,35 @@ __device__ __forceinline__ int gamma_class(uint64_t A, uint64_t B, uint64_t C, b
     return f4_log((int)((a >> k) & 1), (int)((b >> k) & 1));
 }
 
-// Partial Euclid of NUCOMP/NUDUPL: stops once |by| <= L or bx = 0.
+// Partial Euclid of NUCOMP/NUDUPL: stops once |by| <= L or bx = 0.  Here
+// 0 <= bx < by < 2^31 (by is a norm over a gcd), so the loop runs in 32-bit
+// arithmetic; the cofactors x, y stay below by in magnitude.
 __device__ __forceinline__ void nu_partial(int64_t &bx, int64_t &by, int64_t &x, int64_t &y,
                                            int &z, int64_t L) {
     x = 1;
     y = 0;
     z = 0;
+    if (bx >= 0 && by >= 0 && by < 0x7fffffff) {
+        int32_t bx32 = (int32_t)bx, by32 = (int32_t)by, x32 = 1, y32 = 0;
+        while (by32 > L && bx32 != 0) {
+            const int32_t q = by32 / bx32, t = by32 - q * bx32;
+            by32 = bx32;
+            bx32 = t;
+            const int32_t u = y32 - q * x32;
+            y32 = x32;
+            x32 = u;
+            ++z;
+        }
+        bx = bx32;
+        by = by32;
+        x = x32;
+        y = y32;
+        if (z & 1) {
+            by = -by;
+            y = -y;
+        }
+        return;
+    }
     while ((by < 0 ? -by : by) > L && bx != 0) {
         const int64_t q = by / bx, t = by - q * bx;  // bx, by >= 0 here
         by = bx;
