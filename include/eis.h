@@ -163,7 +163,14 @@ int eis_classify_range_log(eis_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *log_
                            int out_on_device, void *stream);
 
 /* *result_out = 1 if d is in E, 0 if d is in D \ E (Section 1, Lemma 1.1(i)).
- * d not in D: EIS_ENOTD and nothing written. */
+ * d not in D (d != 5 mod 8, or p^2 | d for an odd prime p): EIS_ENOTD and
+ * nothing written; d >= EIS_D_LIMIT: EIS_ERANGE; a walk or giant-step
+ * search past its limit: EIS_ESTEPS.  The square-free test spreads the prime
+ * table over the whole GPU; then, in EIS_MODE_PERSISTENT (default), one warp
+ * runs the baby-step giant-step search of Algorithm 1 (composition per
+ * EIS_OPT_GIANT_COMPOSE), and in EIS_MODE_PLAIN one lane walks the half
+ * period.  Synchronous on the context's stream; eis_get_stats reports the
+ * baby and giant steps taken. */
 int eis_is_eisenstein(eis_ctx *ctx, uint64_t d, int *result_out);
 
 /* counts_out[i] = #E cap [lo[i], hi[i]) for i < n, all intervals classified
