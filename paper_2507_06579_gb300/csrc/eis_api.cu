@@ -247,6 +247,7 @@ static void plan_free(eis_plan *p) {
 
 static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t n, int mode,
                       int with_log, eis_plan **out, uint32_t flags = 0) {
+    EisNvtxRange range("eis.plan_build");
     if (flags & ~(uint32_t)(EIS_PLAN_CLASSES | EIS_PLAN_PRIMES)) return EIS_EINVAL;
     if (flags & EIS_PLAN_CLASSES) with_log = 1;
     if (!c || !out || (n && (!lo || !hi))) return EIS_EINVAL;
@@ -380,6 +381,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
 }
 
 static int plan_launch(eis_plan *p, cudaStream_t s) {
+    EisNvtxRange range("eis.plan_launch");
     EIS_CK(cudaSetDevice(p->ctx->device));
     if (!s) s = p->ctx->stream;
     if (p->exec) {
@@ -789,6 +791,7 @@ int eis_plan_destroy(eis_plan *p) {
 }
 
 int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
+    EisNvtxRange range("eis.autotune");
     if (!c || !out || lo >= hi) return EIS_EINVAL;
     if (hi > EIS_D_LIMIT) return EIS_ERANGE;
     struct Setting {
@@ -954,6 +957,7 @@ int eis_classify_range_log(eis_ctx *c, uint64_t lo, uint64_t hi, uint8_t *log_ou
 }
 
 int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
+    EisNvtxRange range("eis.is_eisenstein");
     if (!c || !result_out) return EIS_EINVAL;
     if (d >= EIS_D_LIMIT) return EIS_ERANGE;
     if (d % 8 != 5) return EIS_ENOTD;

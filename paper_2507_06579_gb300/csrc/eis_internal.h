@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "eis.h"
 
 struct eis_ctx_view {
@@ -25,3 +27,13 @@ eis_ctx_view eis_ctx_get_view(eis_ctx *ctx);
 // Account `bytes` of device memory against the context budget; false if over.
 bool eis_ctx_reserve(eis_ctx *ctx, uint64_t bytes);
 void eis_ctx_release(eis_ctx *ctx, uint64_t bytes);
+
+// Host-side NVTX range for the phases a profiler timeline should show
+// (plan build and launch, single queries, autotuning, server batches).  The
+// header-only NVTX API costs nothing when no tool is attached.
+struct EisNvtxRange {
+    explicit EisNvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~EisNvtxRange() { nvtxRangePop(); }
+    EisNvtxRange(const EisNvtxRange &) = delete;
+    EisNvtxRange &operator=(const EisNvtxRange &) = delete;
+};

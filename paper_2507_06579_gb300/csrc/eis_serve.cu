@@ -164,6 +164,7 @@ uint64_t slot_bytes(const eis_server_config &c, uint32_t max_tiles, uint32_t def
 
 // Launch one batch (the slot's items) on the slot's stream.
 bool launch_batch(eis_server *s, Slot &sl) {
+    EisNvtxRange range("eis.server.batch");
     eis_ctx_view cv = eis_ctx_get_view(s->ctx);
     std::sort(sl.items.begin(), sl.items.end(),
               [](const Part &a, const Part &b) { return a.d0 < b.d0; });
