@@ -36,7 +36,10 @@ METRIC = "discriminants classified/s near d=1e11"
 UNIT = "discriminants/s"
 WINDOW = 10**9
 TOP = 10**11
-OPS_PER_BABY_STEP = 11      # int32-equivalent operations of one rho step
+# int32-equivalent operations of one rho step: the add P + s, the quotient,
+# two subtractions, the multiply-add of the Q recurrence, two for the Z/3
+# class, two compares for the centre test and two for loop and exit
+OPS_PER_BABY_STEP = 11
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
