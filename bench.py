@@ -110,18 +110,29 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
+def walk_source_hash():
+    """SHA-1 (16 hex digits) of the walk kernel's sources with comments and
+    blank lines removed, so that only code changes invalidate a record."""
+    import hashlib
+    import re
+    h = hashlib.sha1()
+    for f in ("k_walk.cu", "eis_common.cuh"):
+        src = open(os.path.join(ROOT, "paper_2507_06579_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
+    return h.hexdigest()[:16]
+
+
 def walk_traffic():
     """DRAM bytes per launch of the walk kernel from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
-    import hashlib
+    summary, or None when the kernel's code changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get("k_walk_persistent")
-    h = hashlib.sha1()
-    for f in ("k_walk.cu", "eis_common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2507_06579_gb300", "csrc", f), "rb").read())
-    if not rec or rec.get("source_sha1_16") != h.hexdigest()[:16]:
+    if not rec or rec.get("source_sha1_16") != walk_source_hash():
         return None
     return rec["bytes_per_launch"]
 

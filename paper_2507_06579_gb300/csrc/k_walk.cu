@@ -7,8 +7,13 @@
 //                     when its walk ends, takes the next square-free
 //                     candidate from a global queue (warp-aggregated atomic),
 //                     so lanes stay busy whatever the spread of periods.
-//  k_walk_single      one warp: square-free test of one d against the prime
-//                     table, then the walk in lane 0.
+//  k_sqfree_one       the square-free test of one d spread over a whole grid
+//                     (single queries).
+//  k_walk_single      one warp: the square-free answer of k_sqfree_one (or its
+//                     own scan of the prime table), then the walk in lane 0.
+// All three walkers run the lean step of eis_common.cuh (num = P + s state,
+// class bit from the quotient's parity) and test for the centre once per
+// group of steps.
 #include "eis_common.cuh"
 #include "eis_kernels.h"
 
