@@ -85,3 +85,27 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "oracle.h" not in txt, f
                 assert "from oracle" not in txt, f
+
+
+def test_header_is_plain_c_and_links(libeis, tmp_path):
+    """A C11 program that includes only eis.h compiles without warnings and
+    links against the library (it is not run: that needs a device)."""
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include "eis.h"\n'
+        "int main(void) {\n"
+        "    eis_ctx *ctx;\n"
+        "    uint64_t n = 0;\n"
+        "    int r = 0;\n"
+        "    if (eis_create(&ctx, 0, 0) != EIS_OK) return 1;\n"
+        "    eis_count_range(ctx, 0, 1000001ull, &n);\n"
+        "    eis_is_eisenstein(ctx, 1901, &r);\n"
+        "    eis_destroy(ctx);\n"
+        "    return (int)(n & 1) + r;\n"
+        "}\n")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(E.LIB_PATH)
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", libdir, "-leis_gb300",
+                        "-o", str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
