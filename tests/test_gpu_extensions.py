@@ -50,3 +50,37 @@ def test_class_counts_match_oracle(ctx, orc, lo, hi):
     assert gp == [int((refp == 1).sum()), int((refp == 2).sum()), int((refp == 3).sum())]
     # the E class is the Eisenstein count
     assert got[0] == ctx.count_range(lo, hi)
+
+
+def test_c_program_through_the_abi(tmp_path):
+    """A plain C program (no Python in the loop) counts pi_E(10^8) and asks
+    for 1901 through include/eis.h."""
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    E.build()
+    src = tmp_path / "prog.c"
+    src.write_text(
+        "#include <stdio.h>\n"
+        '#include "eis.h"\n'
+        "int main(void) {\n"
+        "    eis_ctx *ctx;\n"
+        "    int rc = eis_create(&ctx, 0, 0);\n"
+        "    if (rc != EIS_OK) { printf(\"create %d\\n\", rc); return 1; }\n"
+        "    uint64_t n = 0;\n"
+        "    int r = -1;\n"
+        "    rc = eis_count_range(ctx, 0, 100000001ull, &n);\n"
+        "    if (rc == EIS_OK) rc = eis_is_eisenstein(ctx, 1901, &r);\n"
+        "    printf(\"%d %llu %d\\n\", rc, (unsigned long long)n, r);\n"
+        "    eis_destroy(ctx);\n"
+        "    return rc == EIS_OK ? 0 : 2;\n"
+        "}\n")
+    exe = tmp_path / "prog"
+    libdir = os.path.dirname(E.LIB_PATH)
+    cc = subprocess.run(["gcc", "-std=c11", "-Wall", "-I", os.path.join(root, "include"), str(src),
+                         "-L", libdir, "-leis_gb300", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                        capture_output=True, text=True, timeout=120)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert run.returncode == 0, run.stdout + run.stderr
+    assert run.stdout.split() == ["0", "3259668", "1"]
