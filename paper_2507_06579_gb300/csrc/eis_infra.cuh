@@ -31,6 +31,10 @@
 
 namespace eis {
 
+// The ideal arithmetic below is plain integer code that also compiles for
+// the host, where tests run it against an exact walk of the cycle.
+#define EIS_HD __host__ __device__ __forceinline__
+
 struct Ideal {
     int64_t a;  // Q/2
     int64_t b;  // P
@@ -39,7 +43,7 @@ struct Ideal {
 
 // Extended Euclid in 32-bit arithmetic for 0 <= a, b < 2^31 (the ideal norms
 // and their half-sums are below 2^23): returns gcd with x a + y b = gcd.
-__device__ __forceinline__ int64_t egcd32(int32_t a, int32_t b, int64_t &x, int64_t &y) {
+EIS_HD int64_t egcd32(int32_t a, int32_t b, int64_t &x, int64_t &y) {
     int32_t x0 = 1, y0 = 0, x1 = 0, y1 = 1;
     while (b != 0) {
         const int32_t q = a / b;
@@ -61,7 +65,7 @@ __device__ __forceinline__ int64_t egcd32(int32_t a, int32_t b, int64_t &x, int6
 // Extended Euclid: returns gcd(a, b) >= 0 with x a + y b = gcd.  Operands
 // below 2^31 in magnitude take the 32-bit loop on |a|, |b| (the cofactors'
 // signs follow the operands'); the forms' middle coefficients are negative.
-__device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t &x, int64_t &y) {
+EIS_HD int64_t egcd64(int64_t a, int64_t b, int64_t &x, int64_t &y) {
     const int64_t aa = a < 0 ? -a : a, ab = b < 0 ? -b : b;
     if (aa < 0x7fffffff && ab < 0x7fffffff) {
         const int64_t g = egcd32((int32_t)aa, (int32_t)ab, x, y);
@@ -92,12 +96,12 @@ __device__ __forceinline__ int64_t egcd64(int64_t a, int64_t b, int64_t &x, int6
     return a;
 }
 
-__device__ __forceinline__ int64_t mod_pos(int64_t x, int64_t m) {
+EIS_HD int64_t mod_pos(int64_t x, int64_t m) {
     int64_t r = x % m;
     return r < 0 ? r + m : r;
 }
 
-__device__ __forceinline__ int64_t floor_div(int64_t x, int64_t y) {
+EIS_HD int64_t floor_div(int64_t x, int64_t y) {
     int64_t q = x / y;
     if ((x % y != 0) && ((x < 0) != (y < 0))) --q;
     return q;
@@ -108,8 +112,12 @@ __device__ __forceinline__ int64_t floor_div(int64_t x, int64_t y) {
 // and the product), so while it is below 2^20 in magnitude it lies within
 // 0.4 of x/y and its floor is q - 1, q or q + 1; one integer correction each
 // way fixes it.  Larger quotients take the 64-bit division.
-__device__ __forceinline__ int64_t floor_div_fast(int64_t x, int64_t y) {
+EIS_HD int64_t floor_div_fast(int64_t x, int64_t y) {
+#ifdef __CUDA_ARCH__
     const float e = floorf(__fmul_rn((float)x, rcp_approx((float)y)));
+#else
+    const float e = floorf((float)x * (1.0f / (float)y));  // within the same bound
+#endif
     if (fabsf(e) >= 1048576.0f) return floor_div(x, y);
     int64_t q = (int64_t)(int32_t)e;
     const int64_t r = x - q * y;  // floor wants 0 <= r < y (y > 0), y < r <= 0 (y < 0)
@@ -122,17 +130,16 @@ __device__ __forceinline__ int64_t floor_div_fast(int64_t x, int64_t y) {
 }
 
 // Inverse of an odd a modulo 2^64.
-__device__ __forceinline__ uint64_t inv_odd_u64(uint64_t a) {
+EIS_HD uint64_t inv_odd_u64(uint64_t a) {
     uint64_t x = a;  // a * a == 1 (mod 8): 3 correct bits
-#pragma unroll
     for (int i = 0; i < 5; ++i) x *= 2 - a * x;
     return x;
 }
 
 // Primitive part (a3, b3) of the product of [a1,(b1+sqrt d)/2] and
 // [a2,(b2+sqrt d)/2] (both primitive, b odd, 4a | b^2 - d, a < 2^22).
-__device__ __forceinline__ void ideal_compose(int64_t a1, int64_t b1, int64_t a2, int64_t b2,
-                                              int64_t d, int64_t &a3, int64_t &b3) {
+EIS_HD void ideal_compose(int64_t a1, int64_t b1, int64_t a2, int64_t b2,
+                          int64_t d, int64_t &a3, int64_t &b3) {
     if (a1 > a2) {
         int64_t t = a1; a1 = a2; a2 = t;
         t = b1; b1 = b2; b2 = t;
@@ -171,13 +178,13 @@ __device__ __forceinline__ void ideal_compose(int64_t a1, int64_t b1, int64_t a2
     a3 = v1 * v2;
 }
 
-__device__ __forceinline__ bool ideal_is_reduced(int64_t P, int64_t Q, int64_t s) {
+EIS_HD bool ideal_is_reduced(int64_t P, int64_t Q, int64_t s) {
     return Q > 0 && P > 0 && P <= s && s - P < Q && Q <= s + P;
 }
 
 // (d - P^2) / Q exactly, for Q == 2 (mod 4) dividing d - P^2 and a quotient
 // below 2^62 in magnitude.
-__device__ __forceinline__ int64_t exact_quot(int64_t d, int64_t P, int64_t Q) {
+EIS_HD int64_t exact_quot(int64_t d, int64_t P, int64_t Q) {
     const uint64_t X = (uint64_t)d - (uint64_t)P * (uint64_t)P;  // d - P^2 mod 2^64
     const int64_t ha = Q > 0 ? Q / 2 : -(Q / 2);                   // |Q|/2, odd
     const uint64_t m = ((X >> 1) * inv_odd_u64((uint64_t)ha)) & 0x7fffffffffffffffull;
@@ -188,8 +195,8 @@ __device__ __forceinline__ int64_t exact_quot(int64_t d, int64_t P, int64_t Q) {
 // rho until reduced; returns the class gained, or -1 past max_steps.  P must
 // lie within about |Q| + 2^23 of 0 on entry (true of every composition here),
 // which keeps Q_{-1} and every later value below 2^47.
-__device__ __forceinline__ int ideal_reduce(int64_t &P, int64_t &Q, int64_t d, int64_t s,
-                                            int max_steps) {
+EIS_HD int ideal_reduce(int64_t &P, int64_t &Q, int64_t d, int64_t s,
+                        int max_steps) {
     if (ideal_is_reduced(P, Q, s)) return 0;
     int g = 0;
     int64_t Qm = exact_quot(d, P, Q);  // Q_{-1}
@@ -207,8 +214,8 @@ __device__ __forceinline__ int ideal_reduce(int64_t &P, int64_t &Q, int64_t d, i
 }
 
 // reduce(X * Y) with classes; returns false if the reduction ran away.
-__device__ __forceinline__ bool ideal_mul(const Ideal &X, const Ideal &Y, int64_t d, int64_t s,
-                                          Ideal &out) {
+EIS_HD bool ideal_mul(const Ideal &X, const Ideal &Y, int64_t d, int64_t s,
+                      Ideal &out) {
     int64_t a3, b3;
     ideal_compose(X.a, X.b, Y.a, Y.b, d, a3, b3);
     int64_t P = b3, Q = 2 * a3;
@@ -232,15 +239,24 @@ __device__ __forceinline__ bool ideal_mul(const Ideal &X, const Ideal &Y, int64_
 // gamma mod 2O_K.  Only those low bits are needed, so A, B, C are formed in
 // wrapping 64-bit arithmetic.
 
-// log_omega of (x + y omega) for (x, y) != (0, 0) mod 2.
-__device__ __forceinline__ int f4_log(int x, int y) { return y ? (x ? 2 : 1) : 0; }
+// Trailing zero bits of x != 0.
+EIS_HD int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __ffsll((long long)x) - 1;
+#else
+    return __builtin_ctzll(x);
+#endif
+}
 
-__device__ __forceinline__ int gamma_class(uint64_t A, uint64_t B, uint64_t C, bool &ok) {
+// log_omega of (x + y omega) for (x, y) != (0, 0) mod 2.
+EIS_HD int f4_log(int x, int y) { return y ? (x ? 2 : 1) : 0; }
+                  
+                  EIS_HD int gamma_class(uint64_t A, uint64_t B, uint64_t C, bool &ok) {
     const uint64_t a = A - B, b = 2 * B;
-    const int ka = a ? __ffsll((long long)a) - 1 : 64;
-    const int kb = b ? __ffsll((long long)b) - 1 : 64;
+    const int ka = a ? ctz64(a) : 64;
+    const int kb = b ? ctz64(b) : 64;
     const int k = ka < kb ? ka : kb;
-    const int kc = C ? __ffsll((long long)C) - 1 : 64;
+    const int kc = C ? ctz64(C) : 64;
     if (k != kc || k >= 63) {
         ok = false;
         return 0;
@@ -251,8 +267,8 @@ __device__ __forceinline__ int gamma_class(uint64_t A, uint64_t B, uint64_t C, b
 // Partial Euclid of NUCOMP/NUDUPL: stops once |by| <= L or bx = 0.  Here
 // 0 <= bx < by < 2^31 (by is a norm over a gcd), so the loop runs in 32-bit
 // arithmetic; the cofactors x, y stay below by in magnitude.
-__device__ __forceinline__ void nu_partial(int64_t &bx, int64_t &by, int64_t &x, int64_t &y,
-                                           int &z, int64_t L) {
+EIS_HD void nu_partial(int64_t &bx, int64_t &by, int64_t &x, int64_t &y,
+                       int &z, int64_t L) {
     x = 1;
     y = 0;
     z = 0;
@@ -294,9 +310,9 @@ __device__ __forceinline__ void nu_partial(int64_t &bx, int64_t &by, int64_t &x,
 
 // NUCOMP (Algorithm 2).  Returns false if a division that must be exact is
 // not (never expected).
-__device__ __forceinline__ bool nucomp(int64_t u1, int64_t v1, int64_t w1, int64_t u2, int64_t v2,
-                                       int64_t w2, int64_t L, int64_t &u3, int64_t &v3,
-                                       int64_t &w3, uint64_t &A, uint64_t &B, uint64_t &C) {
+EIS_HD bool nucomp(int64_t u1, int64_t v1, int64_t w1, int64_t u2, int64_t v2,
+                   int64_t w2, int64_t L, int64_t &u3, int64_t &v3,
+                   int64_t &w3, uint64_t &A, uint64_t &B, uint64_t &C) {
     if (w1 < w2) {
         int64_t t = u1; u1 = u2; u2 = t;
         t = v1; v1 = v2; v2 = t;
@@ -368,9 +384,9 @@ __device__ __forceinline__ bool nucomp(int64_t u1, int64_t v1, int64_t w1, int64
 }
 
 // NUDUPL (Algorithm 3).
-__device__ __forceinline__ bool nudupl(int64_t u, int64_t v, int64_t w, int64_t L, int64_t &u3,
-                                       int64_t &v3, int64_t &w3, uint64_t &A, uint64_t &B,
-                                       uint64_t &C) {
+EIS_HD bool nudupl(int64_t u, int64_t v, int64_t w, int64_t L, int64_t &u3,
+                   int64_t &v3, int64_t &w3, uint64_t &A, uint64_t &B,
+                   uint64_t &C) {
     int64_t xx, yy;
     const int64_t G = egcd64(u, v, xx, yy);  // xx u + yy v = G
     const int64_t By = u / G, Dy = v / G;
@@ -409,8 +425,8 @@ __device__ __forceinline__ bool nudupl(int64_t u, int64_t v, int64_t w, int64_t 
 }
 
 // NUCOMPchoose (Algorithm 4) + reduction: reduce(X * Y) with classes.
-__device__ __forceinline__ bool ideal_mul_nucomp(const Ideal &X, const Ideal &Y, int64_t d,
-                                                 int64_t s, int64_t L, Ideal &out) {
+EIS_HD bool ideal_mul_nucomp(const Ideal &X, const Ideal &Y, int64_t d,
+                             int64_t s, int64_t L, Ideal &out) {
     int64_t u1 = 2 * X.a, u2 = 2 * Y.a;  // Q (positive for reduced ideals)
     int64_t v1 = mod_pos(X.b, u1), v2 = mod_pos(Y.b, u2);
     int64_t P, Q;
