@@ -27,6 +27,7 @@ int main() {
         const bool okN = eis::ideal_mul_nucomp(X, Y, d, s, L, N);
         std::printf("%d %lld %lld %d %d %lld %lld %d\n", okT ? 1 : 0, (long long)T.a, (long long)T.b,
                     T.g, okN ? 1 : 0, (long long)N.a, (long long)N.b, N.g);
+        std::fflush(stdout);  // one answer per line, for interactive use
     }
     return 0;
 }

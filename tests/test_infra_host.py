@@ -101,3 +101,79 @@ def test_products_land_on_the_cycle_with_their_class(infra_host, orc, lo, hi):
             assert abs(dj - dsum) <= math.log(d), (d, i, k, j, dj, dsum)
         n_small += min(i, k) < 3
     assert len(rows) - 1 == len(expect) and n_small > 0
+
+
+class _Composer:
+    """reduce(X * Y) through the host driver, one product per line."""
+
+    def __init__(self, exe):
+        self.p = subprocess.Popen([exe], stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True,
+                                  bufsize=1)
+
+    def mul(self, d, X, Y, nucomp):
+        self.p.stdin.write("%d %d %d %d %d %d %d\n" % ((d,) + X + Y))
+        self.p.stdin.flush()
+        okT, aT, bT, gT, okN, aN, bN, gN = map(int, self.p.stdout.readline().split())
+        ok, out = (okN, (aN, bN, gN)) if nucomp else (okT, (aT, bT, gT))
+        assert ok == 1
+        return out
+
+    def close(self):
+        self.p.stdin.close()
+        self.p.wait(timeout=60)
+
+
+def _search_log(comp, d, N, nucomp):
+    """Algorithm 1 as the giant-step kernel runs it: baby states 1..N in a
+    table under direct keys (Q_j, P_j) and mirror keys (Q_j, P_{j+1}), O_K as
+    (2, P_1); G = state N+1; lane t starts at G^(t+2) and strides by G^32;
+    the first hit in (round, lane) order gives log eps = g(mu) + S_j (mirror)
+    or g(mu) - S_j (direct).  None when the centre comes within N steps."""
+    s = math.isqrt(d)
+    P = 2 * ((1 + s) // 2) - 1
+    Q = (d - P * P) // 2
+    table = {(2, P): ("d", 0)}
+    S = _c(P)
+    for _ in range(N):
+        q = (P + s) // Q
+        Pn = q * Q - P
+        Qn = (d - Pn * Pn) // Q
+        if Qn == Q or Pn == P:
+            return None
+        table.setdefault((Q, P), ("d", S % 3))
+        table.setdefault((Q, Pn), ("m", S % 3))
+        S += _c(Pn)
+        P, Q = Pn, Qn
+    G = (Q // 2, P, S % 3)
+    mu = [comp.mul(d, G, G, nucomp)]
+    for _ in range(31):
+        mu.append(comp.mul(d, mu[-1], G, nucomp))
+    stride = comp.mul(d, mu[29], G, nucomp)  # G^32 = G^31 * G
+    for _ in range(100000):
+        for a, b, g in mu:
+            hit = table.get((2 * a, b))
+            if hit:
+                kind, Sj = hit
+                return (g + Sj) % 3 if kind == "m" else (g - Sj) % 3
+        mu = [comp.mul(d, m, stride, nucomp) for m in mu]
+    raise AssertionError("no hit")
+
+
+@pytest.mark.parametrize("nucomp", [False, True], ids=["textbook", "nucomp"])
+def test_giant_step_search_model_matches_oracle(infra_host, orc, nucomp):
+    rng = np.random.default_rng(31 + nucomp)
+    comp = _Composer(infra_host)
+    try:
+        n = 0
+        while n < 12:
+            d = int(rng.integers(10**9 // 8, 10**11 // 8)) * 8 + 5
+            if not orc.in_D(d):
+                continue
+            got = _search_log(comp, d, 64, nucomp)
+            if got is None:
+                continue  # short period: the baby phase ends it
+            rc, theta, _ = orc.walk_mod2(d)
+            assert rc == 0 and got == theta - 1, (d, got, theta)
+            n += 1
+    finally:
+        comp.close()
