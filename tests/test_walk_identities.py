@@ -182,3 +182,27 @@ def test_exact_division_by_the_2adic_inverse():
                 if (d - Pk * Pk) % Q == 0:
                     assert _exact_quot(d, Pk, Q) == (d - Pk * Pk) // Q
                     assert _exact_quot(d, Pk, -Q) == (d - Pk * Pk) // -Q
+
+
+@pytest.mark.parametrize("top", [FAST_D_LIMIT + 10**9, 10**13, D_LIMIT - 1])
+def test_corrected_quotient_up_to_2_44(top):
+    """Above the fast limit the walk floors num * rcp(Q) onto 2^23 - 1/2 with
+    num = P + s: the result is q or q - 1, the remainder num - q' Q lies in
+    [0, 2Q), and one compare with Q gives q."""
+    rng = np.random.default_rng(top % 83 + 9)
+    M = 1 << 23
+    for d in _nonsquare_5mod8(rng, top - 10**9, top, 6):
+        s = math.isqrt(d)
+        for P, Q, q, _, _ in _rho(d, 300)[1:]:
+            num = P + s
+            assert num < M  # exact in fp32, as is every product below
+            for r in _f32_rcp_candidates(Q):
+                # fma rounded toward -inf onto the integer grid of [2^23, 2^24)
+                qm = math.floor(Fraction(num) * Fraction(float(r)) + M - Fraction(1, 2))
+                qe = qm - M
+                assert qe in (q, q - 1), (d, P, Q)
+                rem = num - qe * Q
+                assert 0 <= rem < 2 * Q
+                if rem >= Q:
+                    qe += 1
+                assert qe == q
