@@ -88,6 +88,7 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int), ("sm_count", ctypes.c_int)]
 
     def as_dict(self):
+        """The fields as a plain dict."""
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
@@ -102,6 +103,7 @@ class TuneResult(ctypes.Structure):
                 ("ms_default", ctypes.c_double), ("trials", ctypes.c_int32)]
 
     def as_dict(self):
+        """The fields as a plain dict."""
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
@@ -117,6 +119,7 @@ class ServerStats(ctypes.Structure):
         "max_batch_parts", "pending_parts", "reserved_bytes")]
 
     def as_dict(self):
+        """The fields as a plain dict."""
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
@@ -225,9 +228,12 @@ class Plan:
         return out[: 3 * self.n].reshape(self.n, 3)
 
     def launch(self, stream=None):
+        """Enqueue one full pass (the plan's CUDA graph) on `stream`, by default the context's
+        stream; asynchronous, as eis_plan_launch."""
         _check(lib().eis_plan_launch(self.handle, _stream_handle(stream)), "eis_plan_launch")
 
     def counts(self):
+        """Per-interval #E (d in E) of the last launch."""
         out = np.zeros(max(self.n, 1), dtype=np.uint64)
         _check(lib().eis_plan_counts(self.handle, out.ctypes.data), "eis_plan_counts")
         return out[: self.n]
@@ -239,6 +245,7 @@ class Plan:
         return out[: self.n]
 
     def stats(self) -> dict:
+        """Counts and device times of the last launch (eis_plan_stats)."""
         st = Stats()
         _check(lib().eis_plan_stats(self.handle, ctypes.byref(st)), "eis_plan_stats")
         return st.as_dict()
@@ -262,6 +269,7 @@ class Plan:
         return f[:tot], s[:tot]
 
     def destroy(self):
+        """Free the plan's device buffers and graph (idempotent)."""
         if self.handle:
             lib().eis_plan_destroy(self.handle)
             self.handle = None
@@ -288,18 +296,21 @@ class Server:
         self.handle = h
 
     def submit_count(self, lo: int, hi: int) -> int:
+        """Queue #E over [lo, hi); returns the request id."""
         rid = ctypes.c_uint64()
         _check(lib().eis_server_submit(self.handle, EIS_REQ_COUNT, lo, hi, ctypes.byref(rid)),
                "eis_server_submit")
         return int(rid.value)
 
     def submit_member(self, d: int) -> int:
+        """Queue the membership query 'is d in E'; returns the request id."""
         rid = ctypes.c_uint64()
         _check(lib().eis_server_submit(self.handle, EIS_REQ_MEMBER, d, d + 1, ctypes.byref(rid)),
                "eis_server_submit")
         return int(rid.value)
 
     def poll(self, rid: int) -> bool:
+        """True once request rid has finished (does not wait)."""
         done = ctypes.c_int()
         _check(lib().eis_server_poll(self.handle, rid, ctypes.byref(done)), "eis_server_poll")
         return bool(done.value)
@@ -313,9 +324,11 @@ class Server:
         return rc, int(res.value), float(lat.value)
 
     def cancel(self, rid: int):
+        """Drop request rid if it has not finished."""
         _check(lib().eis_server_cancel(self.handle, rid), "eis_server_cancel")
 
     def stats(self) -> dict:
+        """Server counters: requests, batches, parts, reserved memory."""
         st = ServerStats()
         _check(lib().eis_server_stats(self.handle, ctypes.byref(st)), "eis_server_stats")
         return st.as_dict()
@@ -338,6 +351,7 @@ class Server:
                 "wall_s": float(wall.value)}
 
     def close(self):
+        """Stop the server and free its slots (idempotent)."""
         if getattr(self, "handle", None):
             lib().eis_server_destroy(self.handle)
             self.handle = None
@@ -367,6 +381,7 @@ class Context:
             self.set_option(EIS_OPT_MODE, mode)
 
     def close(self):
+        """Release the context and every device resource it owns (idempotent)."""
         if getattr(self, "handle", None):
             lib().eis_destroy(self.handle)
             self.handle = None
@@ -385,20 +400,24 @@ class Context:
 
     # -- options / stats
     def set_option(self, key: int, value: int):
+        """Set an EIS_OPT_* option (raises EisError on an invalid value)."""
         _check(lib().eis_set_option(self.handle, key, int(value)), "eis_set_option")
 
     def get_option(self, key: int) -> int:
+        """Current value of an EIS_OPT_* option."""
         v = ctypes.c_int64()
         _check(lib().eis_get_option(self.handle, key, ctypes.byref(v)), "eis_get_option")
         return int(v.value)
 
     def stats(self) -> dict:
+        """Counts, steps and times of the context's last call (eis_get_stats)."""
         st = Stats()
         _check(lib().eis_get_stats(self.handle, ctypes.byref(st)), "eis_get_stats")
         return st.as_dict()
 
     # -- entry points
     def count_range(self, lo: int, hi: int) -> int:
+        """#E over the half-open range [lo, hi)."""
         out = ctypes.c_uint64()
         _check(lib().eis_count_range(self.handle, lo, hi, ctypes.byref(out)), "eis_count_range")
         return int(out.value)
@@ -428,6 +447,8 @@ class Context:
         return flags_out, sqfree_out, int(cnt.value)
 
     def classify_range_u8(self, lo: int, hi: int, codes_out=None, stream=None):
+        """One byte per candidate d == 5 (mod 8) of [lo, hi): 0 not in D, 1 in D \\ E, 2 in E.
+        Returns (codes, #E); a torch CUDA tensor as codes_out is written on the device."""
         n, _ = num_candidates(lo, hi)
         cnt = ctypes.c_uint64()
         if codes_out is None:
@@ -442,6 +463,7 @@ class Context:
         return codes_out, int(cnt.value)
 
     def classify_range_log(self, lo: int, hi: int, stream=None):
+        """One byte per candidate: 0 not in D, else 1 + log_omega(eps_d mod 2O_K)."""
         n, _ = num_candidates(lo, hi)
         out = np.zeros(max(n, 1), dtype=np.uint8)
         _check(lib().eis_classify_range_log(self.handle, lo, hi, out.ctypes.data, 0,
@@ -449,11 +471,13 @@ class Context:
         return out[:n]
 
     def is_eisenstein(self, d: int) -> bool:
+        """True if d is in E; raises EisError with code EIS_ENOTD if d is not in D."""
         r = ctypes.c_int()
         _check(lib().eis_is_eisenstein(self.handle, d, ctypes.byref(r)), "eis_is_eisenstein")
         return bool(r.value)
 
     def count_batch(self, los, his):
+        """#E of each range [los[i], his[i]) in one persistent launch."""
         lo = _u64_array(los)
         hi = _u64_array(his)
         assert lo.shape == hi.shape
@@ -492,6 +516,7 @@ class Context:
         return dict(r, cached=False)
 
     def plan_create(self, los, his, mode: int = EIS_MODE_PERSISTENT, flags: int = 0) -> Plan:
+        """A reusable plan over the ranges [los[i], his[i]) (see Plan)."""
         return Plan(self, los, his, mode, flags)
 
     def class_counts(self, lo: int, hi: int, primes_only: bool = False):
