@@ -9,10 +9,22 @@ comes from CUDA events recorded by the plan on its launch stream; L2 is
 flushed (a 512 MiB write) between steps.
 
 Besides the headline ``value`` (persistent work-stealing form) the JSON line
-carries the plain one-launch-per-2^24-block kernel on the same window
-(``plain``), an end-to-end figure through eis_classify_range with host
-buffers (``e2e``), the ALU roofline of the walk kernel, sampled SM clocks,
-and the CPU oracle timed on a bounded sample (``cpu_baseline``).
+carries:
+
+* ``plain``: the one-launch-per-2^24-block kernel on the same window;
+* ``batched``: 4096 seeded intervals in one persistent launch, and the same
+  intervals through the plain kernel;
+* ``serving``: p50/p99 latency and throughput of the continuous-batching
+  server under Poisson arrivals at 10 to 10^4 requests/s;
+* ``membership``: single-query latency through eis_is_eisenstein (giant-step
+  kernel with either composition, and the single-lane walk);
+* ``e2e``: the same metric through eis_classify_range with host buffers;
+* ``roofline``: the walk kernel against the derived integer-issue peak;
+* ``cpu_baseline``: the CPU oracle timed on a bounded sample;
+* ``clocks``: SM clocks and throttle reasons sampled during the timed steps.
+
+Legs can be shortened or skipped (--plain-steps, --batched-steps,
+--serve-seconds, --no-e2e, --no-cpu-baseline, --no-autotune, --window).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
