@@ -8,7 +8,6 @@ the same pins (first case).  Everything runs on the CPU.
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
