@@ -53,6 +53,9 @@ TOP = 10**11
 # class, two compares for the centre test and two for loop and exit
 OPS_PER_BABY_STEP = 11
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# offered request rates of the serving leg (req/s) and the cap on requests per rate
+SERVE_RATES = (10.0, 100.0, 1000.0, 3000.0, 10000.0, 30000.0, 100000.0)
+SERVE_MAX_REQUESTS = 100000
 
 
 def log(*a):
@@ -345,8 +348,11 @@ def main():
         from paper_2507_06579_gb300 import workloads as W
         rates = []
         with E.Server(ctx) as srv:
-            for rate in (10.0, 100.0, 1000.0, 3000.0, 10000.0):
-                n = int(min(max(rate * args.serve_seconds, 20), 30000))
+            for rate in SERVE_RATES:
+                # at least 1000 requests per rate (300 at 10 req/s, 30 s of
+                # arrivals), so that p99 is not the sample's maximum
+                n = int(min(max(rate * args.serve_seconds, 300 if rate < 100 else 1000),
+                            SERVE_MAX_REQUESTS))
                 reqs = W.serving_stream(n, rate, seed=5)
                 out = srv.replay([r[0] for r in reqs],
                                  [E.EIS_REQ_MEMBER if r[1] == "member" else E.EIS_REQ_COUNT
@@ -360,6 +366,10 @@ def main():
                               "max_ms": float(lat.max()),
                               "throughput_rps": n / out["wall_s"], "wall_s": out["wall_s"]})
             sst = srv.stats()
+        # saturation: the first offered rate the server no longer keeps up with
+        # (throughput below 95% of the offered rate); its throughput is the
+        # server's capacity on this mix
+        sat = next((r for r in rates if r["throughput_rps"] < 0.95 * r["rate_rps"]), None)
         serving = {"workload": "Poisson arrivals, 90% counts [a, a+L) with a log-uniform in "
                                "[1e6, 1e12], L log-uniform in [1e2, 1e6]; 10% membership "
                                "queries on d == 5 mod 8 below 1e12 (not-square-free d answer "
@@ -367,7 +377,13 @@ def main():
                    "server": "4 slots x 2^22 candidates, continuous batching; walks past "
                              "131072 baby steps and membership queries go to the warp-per-d "
                              "giant-step kernel",
-                   "rates": rates, "batches": sst["batches"],
+                   "rates": rates,
+                   "saturation": ({"offered_rps": sat["rate_rps"],
+                                   "throughput_rps": sat["throughput_rps"]} if sat else
+                                  {"offered_rps": None,
+                                   "note": "kept up with every offered rate up to %g req/s"
+                                           % rates[-1]["rate_rps"]}),
+                   "batches": sst["batches"], "deferred": sst["deferred"],
                    "max_batch_parts": sst["max_batch_parts"]}
 
     # single membership queries near 1e12 through eis_is_eisenstein: the
@@ -446,8 +462,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "dtype_note": "integers below 2^23 carried exactly in fp32 "
-                                              "registers; sieve and set-up in u64",
+                "dtype": "int (exact; < 2^23 in fp32 registers)",
+                "dtype_note": "every value is an integer (or integer + 1/2) below 2^23, "
+                              "carried exactly in fp32 registers with exact adds, "
+                              "multiply-adds and a directed-rounding quotient; sieve, set-up "
+                              "and giant steps in u64/i64; results are bit-exact integers",
                 "data": "synthetic",
                 "config": {"workload": "all square-free d == 5 mod 8 in [1e11-%.0e, 1e11] "
                                        "(per rank: its own window below 1e11)" % args.window,

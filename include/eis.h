@@ -78,6 +78,10 @@ extern "C" {
                                   /* the giant-step kernel (0 = never)        */
 #define EIS_OPT_GIANT_STRIDE 7   /* giant-step stride in baby steps (0: auto) */
 #define EIS_OPT_GIANT_COMPOSE 8  /* giant-step composition: EIS_COMPOSE_*      */
+#define EIS_OPT_MEM_BUDGET 9     /* read-only: the context's device-memory    */
+                                 /* budget in bytes                           */
+#define EIS_OPT_MEM_IN_USE 10    /* read-only: bytes charged to the budget    */
+                                 /* (context tables, live plans and servers)  */
 
 /* Giant-step compositions (EIS_OPT_GIANT_COMPOSE). */
 #define EIS_COMPOSE_TEXTBOOK 0 /* product of forms, then rho until reduced      */
@@ -210,12 +214,16 @@ int eis_autotune(eis_ctx *ctx, uint64_t lo, uint64_t hi, eis_tune_result *out);
 #define EIS_NOALLOC_MAX_CANDIDATES (((uint64_t)1) << 20)
 
 /* The paper has no counterpart to this entry point: it exists for callers
- * that must not allocate device memory -- code running inside a host
- * callback or an allocator hook, a process whose GPU memory is owned by
- * another framework's pool, or a real-time loop that forbids allocation after
- * start-up.  Such callers cannot call eis_create (it allocates), so this call
- * takes no context and calls no cudaMalloc, cudaFree or any allocating
- * library routine.
+ * that must not allocate device memory -- an allocator hook (a cudaMalloc
+ * inside it would recurse into the allocator it implements), a process whose
+ * GPU memory is owned by another framework's pool (an allocation behind the
+ * pool's back can fail or break its accounting), or a real-time loop that
+ * forbids allocation after start-up.  Such callers cannot call eis_create (it
+ * allocates), so this call takes no context and calls no cudaMalloc, cudaFree
+ * or any allocating library routine.  It does make other CUDA runtime calls
+ * (memsets, kernel launches, one copy, a stream synchronisation), so it may
+ * not be called from a host function enqueued with cudaLaunchHostFunc, where
+ * CUDA calls are not allowed.
  *
  * It classifies the candidates of [lo, hi) on `device` like
  * eis_classify_range (same bit layout):
@@ -225,7 +233,11 @@ int eis_autotune(eis_ctx *ctx, uint64_t lo, uint64_t hi, eis_tune_result *out);
  *   stream     : cudaStream_t, NULL for the legacy default stream
  * It returns after the results are complete.  More than
  * EIS_NOALLOC_MAX_CANDIDATES candidates give EIS_ETOOLARGE (nothing written);
- * hi above EIS_D_LIMIT gives EIS_ERANGE.
+ * hi above EIS_D_LIMIT gives EIS_ERANGE.  The caller's current device is the
+ * same on return as on entry.  The call checks each CUDA call's own return
+ * code and never reads or clears an error the caller left pending; when one
+ * of its own calls fails it returns EIS_EDEVICE and that error stays pending
+ * in the thread's CUDA error state, as for any failed runtime call.
  *
  * Its scratch (survivor queue, counters, a bitmap when sqfree_out is NULL,
  * about 4.2 MB) is one fixed array in the library's device memory, which every
@@ -318,6 +330,11 @@ typedef struct {
                               /* long period; 0xffffffff: never               */
     uint32_t giant_max;       /* at most this many walks per batch go to the     */
                               /* giant-step kernel (0: slot_candidates / 8)      */
+    uint32_t fail_launches;   /* test hook (0): the first n batch launches fail  */
+                              /* on the host before anything is enqueued, as a   */
+                              /* rejected launch would; their requests complete  */
+                              /* with EIS_EDEVICE and the server stops taking    */
+                              /* new batches                                     */
 } eis_server_config;
 
 typedef struct {
@@ -329,6 +346,8 @@ typedef struct {
     uint64_t max_batch_parts;
     uint64_t pending_parts;
     uint64_t reserved_bytes;  /* device memory of the slots */
+    uint64_t deferred;        /* walks of range parts handed to the giant-step */
+                              /* kernel after giant_after baby steps           */
 } eis_server_counters;
 
 /* Start a server on ctx's device.  Device memory for `slots` batches is

@@ -63,6 +63,8 @@ EIS_OPT_USE_GRAPH = 5
 EIS_OPT_GIANT_THRESHOLD = 6
 EIS_OPT_GIANT_STRIDE = 7
 EIS_OPT_GIANT_COMPOSE = 8
+EIS_OPT_MEM_BUDGET = 9
+EIS_OPT_MEM_IN_USE = 10
 EIS_COMPOSE_TEXTBOOK = 0
 EIS_COMPOSE_NUCOMP = 1
 
@@ -110,13 +112,14 @@ class TuneResult(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("slot_candidates", ctypes.c_uint64),
                 ("slot_requests", ctypes.c_uint32), ("max_pending", ctypes.c_uint32),
-                ("giant_after", ctypes.c_uint32), ("giant_max", ctypes.c_uint32)]
+                ("giant_after", ctypes.c_uint32), ("giant_max", ctypes.c_uint32),
+                ("fail_launches", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "requests_submitted", "requests_done", "rejected", "batches", "parts",
-        "max_batch_parts", "pending_parts", "reserved_bytes")]
+        "max_batch_parts", "pending_parts", "reserved_bytes", "deferred")]
 
     def as_dict(self):
         """The fields as a plain dict."""
@@ -286,10 +289,10 @@ class Server:
 
     def __init__(self, ctx: "Context", slots: int = 0, slot_candidates: int = 0,
                  slot_requests: int = 0, max_pending: int = 0, giant_after: int = 0,
-                 giant_max: int = 0):
+                 giant_max: int = 0, fail_launches: int = 0):
         self.ctx = ctx
         cfg = ServerConfig(slots, slot_candidates, slot_requests, max_pending, giant_after,
-                           giant_max)
+                           giant_max, fail_launches)
         h = ctypes.c_void_p()
         _check(lib().eis_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)),
                "eis_server_create")

@@ -3,6 +3,7 @@
 // convenience calls.  All device memory of a pipeline is allocated when the
 // plan is created; eis_plan_launch only enqueues kernels (or one graph).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,7 +36,10 @@ struct eis_ctx {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     uint64_t budget = 0;
-    uint64_t in_use = 0;
+    // Device bytes charged against the budget: the context's tables, every
+    // live plan and every live server.  Atomic, because a server's dispatcher
+    // thread and plan builds on other threads may reserve at the same time.
+    std::atomic<uint64_t> in_use{0};
     uint32_t *d_primes = nullptr;
     uint64_t *d_sqtab = nullptr;  // per odd prime p: (p^2)^(-1) mod 2^64, floor((2^64-1)/p^2)
     uint32_t nprimes = 0;
@@ -96,14 +100,30 @@ struct eis_plan {
 
 // ------------------------------------------------------------------ helpers
 
+// Charge `bytes` to the context's budget; false (nothing charged) if they do
+// not fit.
+static bool ctx_reserve(eis_ctx *c, uint64_t bytes) {
+    uint64_t cur = c->in_use.load();
+    do {
+        if (bytes > c->budget || cur > c->budget - bytes) return false;
+    } while (!c->in_use.compare_exchange_weak(cur, cur + bytes));
+    return true;
+}
+
+static void ctx_release(eis_ctx *c, uint64_t bytes) {
+    uint64_t cur = c->in_use.load();
+    while (!c->in_use.compare_exchange_weak(cur, cur - std::min(cur, bytes))) {
+    }
+}
+
 static int plan_alloc(eis_plan *p, void **ptr, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    if (p->ctx->in_use + bytes > p->ctx->budget) return EIS_ENOMEM;
+    if (!ctx_reserve(p->ctx, bytes)) return EIS_ENOMEM;
     if (cudaMalloc(ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
+        ctx_release(p->ctx, bytes);
         return EIS_ENOMEM;
     }
-    p->ctx->in_use += bytes;
     p->bytes += bytes;
     return EIS_OK;
 }
@@ -128,7 +148,8 @@ static std::vector<uint32_t> odd_primes_below(uint32_t n) {
 // Bytes a plan needs per candidate: survivor queue (4) + two bitmaps (1/4),
 // plus the optional per-candidate log byte.
 static uint64_t max_chunk_cands(const eis_ctx *c, int with_log) {
-    const uint64_t free_b = c->budget > c->in_use ? c->budget - c->in_use : 0;
+    const uint64_t used = c->in_use.load();
+    const uint64_t free_b = c->budget > used ? c->budget - used : 0;
     uint64_t m = free_b / (5 + (uint64_t)with_log + 1);
     m = std::min<uint64_t>(m, (uint64_t)1 << 31);
     m -= m % kTileCands;
@@ -241,7 +262,7 @@ static void plan_free(eis_plan *p) {
                     p->d_defer, p->d_cls};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    if (p->ctx) p->ctx->in_use -= std::min(p->ctx->in_use, p->bytes);
+    if (p->ctx) ctx_release(p->ctx, p->bytes);
     delete p;
 }
 
@@ -507,13 +528,9 @@ void eis_giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n) {
     log2n = std::min(log2n, kGiantMaxLog2);
 }
 
-bool eis_ctx_reserve(eis_ctx *c, uint64_t bytes) {
-    if (c->in_use + bytes > c->budget) return false;
-    c->in_use += bytes;
-    return true;
-}
+bool eis_ctx_reserve(eis_ctx *c, uint64_t bytes) { return ctx_reserve(c, bytes); }
 
-void eis_ctx_release(eis_ctx *c, uint64_t bytes) { c->in_use -= std::min(c->in_use, bytes); }
+void eis_ctx_release(eis_ctx *c, uint64_t bytes) { ctx_release(c, bytes); }
 
 // ------------------------------------------------------------------ C-ABI
 
@@ -564,6 +581,12 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
     }
     std::vector<uint32_t> pr = odd_primes_below(1u << 22);
     c->nprimes = (uint32_t)pr.size();
+    // Every table of the context is charged once: primes, the square-free
+    // test table (16 B per prime), the single-query words.
+    if (!ctx_reserve(c, pr.size() * 4 + pr.size() * 16 + 4 * sizeof(int) + 64)) {
+        eis_destroy(c);
+        return EIS_ENOMEM;
+    }
     if (cudaMalloc(&c->d_primes, pr.size() * 4) != cudaSuccess ||
         cudaMalloc(&c->d_single, 4 * sizeof(int)) != cudaSuccess) {
         eis_destroy(c);
@@ -585,13 +608,11 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
             eis_destroy(c);
             return EIS_ENOMEM;
         }
-        c->in_use += tab.size() * 8;
     }
     if (cudaMalloc(&c->d_query, 64) != cudaSuccess) {
         eis_destroy(c);
         return EIS_ENOMEM;
     }
-    c->in_use = pr.size() * 4 + 4 * sizeof(int) + 64;
     if (cudaFuncSetAttribute(k_giant, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(8u << kGiantMaxLog2)) != cudaSuccess) {
         eis_destroy(c);
@@ -672,6 +693,8 @@ int eis_get_option(eis_ctx *c, int key, int64_t *v) {
         case EIS_OPT_GIANT_THRESHOLD: *v = c->giant_threshold; return EIS_OK;
         case EIS_OPT_GIANT_STRIDE: *v = c->giant_stride; return EIS_OK;
         case EIS_OPT_GIANT_COMPOSE: *v = c->giant_compose; return EIS_OK;
+        case EIS_OPT_MEM_BUDGET: *v = (int64_t)c->budget; return EIS_OK;
+        case EIS_OPT_MEM_IN_USE: *v = (int64_t)c->in_use.load(); return EIS_OK;
         default: return EIS_EINVAL;
     }
 }

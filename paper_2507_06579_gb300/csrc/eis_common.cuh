@@ -300,6 +300,47 @@ __device__ __forceinline__ uint64_t cand_to_d(const Seg *__restrict__ segs, uint
     return segs[lo].d0 + 8 * (cand - segs[lo].cand0);
 }
 
+// Block-wide sum of one value per thread (valid in thread 0).
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    uint32_t s = 0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// Exclusive block scan of one value per thread; returns the prefix and
+// writes the block total to *total (all threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *red, uint32_t *total) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (l >= o) x += y;
+    }
+    __syncthreads();
+    if (l == 31) red[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (l < nw) ? red[l] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (l >= o) s += y;
+        }
+        if (l < nw) red[l] = s;  // inclusive scan of warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_prefix = (w > 0) ? red[w - 1] : 0;
+    *total = red[nw - 1];
+    return warp_prefix + x - v;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -67,6 +67,7 @@ struct Slot {
     Tile *h_tiles = nullptr;
     unsigned long long *h_counts = nullptr;
     int *h_status = nullptr;
+    uint32_t *h_ctr = nullptr;   // the batch's counters: [2] walks handed to k_giant
     // membership queries of the batch (one warp each in k_giant)
     uint64_t *d_mem_d = nullptr, *h_mem_d = nullptr;
     int8_t *d_mem_out = nullptr, *h_mem_out = nullptr;
@@ -101,6 +102,7 @@ struct eis_server {
     std::thread th;
     eis_server_counters st{};
     bool failed = false;
+    uint32_t fail_left = 0;  // eis_server_config.fail_launches still to fake
 };
 
 namespace {
@@ -128,6 +130,7 @@ int slot_alloc(eis_server *s, Slot &sl) {
               cudaHostAlloc(&sl.h_tiles, s->max_tiles * sizeof(Tile), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&sl.h_counts, (2 * S + 1) * sizeof(unsigned long long), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&sl.h_status, sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&sl.h_ctr, 16, cudaHostAllocDefault) == cudaSuccess &&
               cudaMalloc(&sl.d_mem_d, S * sizeof(uint64_t)) == cudaSuccess &&
               cudaMalloc(&sl.d_mem_out, S) == cudaSuccess &&
               cudaMalloc(&sl.d_mem_ctl, 64) == cudaSuccess &&
@@ -148,7 +151,8 @@ void slot_free(Slot &sl) {
                    sl.d_mem_d, sl.d_mem_out, sl.d_mem_ctl, sl.d_defer};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *host[] = {sl.h_segs, sl.h_tiles, sl.h_counts, sl.h_status, sl.h_mem_d, sl.h_mem_out};
+    void *host[] = {sl.h_segs, sl.h_tiles, sl.h_counts, sl.h_status, sl.h_ctr, sl.h_mem_d,
+                    sl.h_mem_out};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     if (sl.done_ev) cudaEventDestroy(sl.done_ev);
@@ -162,10 +166,17 @@ uint64_t slot_bytes(const eis_server_config &c, uint32_t max_tiles, uint32_t def
            (uint64_t)c.slot_requests * (sizeof(Seg) + 16 + 9) + 320;
 }
 
-// Launch one batch (the slot's items) on the slot's stream.
+// Launch one batch (the slot's items) on the slot's stream.  False when any
+// call fails; the batch's results are then not to be read.
 bool launch_batch(eis_server *s, Slot &sl) {
     EisNvtxRange range("eis.server.batch");
+    if (s->fail_left > 0) {  // test hook: fail before anything is enqueued
+        --s->fail_left;
+        return false;
+    }
     eis_ctx_view cv = eis_ctx_get_view(s->ctx);
+    bool ok = true;
+    auto ck = [&ok](cudaError_t e) { ok &= (e == cudaSuccess); };
     std::sort(sl.items.begin(), sl.items.end(),
               [](const Part &a, const Part &b) { return a.d0 < b.d0; });
     uint64_t cur = 0;
@@ -181,13 +192,13 @@ bool launch_batch(eis_server *s, Slot &sl) {
     const uint32_t nseg = (uint32_t)sl.items.size();
     const uint64_t nwords = cur / 32;
     cudaStream_t st = sl.stream;
-    cudaMemcpyAsync(sl.d_segs, sl.h_segs, nseg * sizeof(Seg), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.d_tiles, sl.h_tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(sl.d_flags, 0, nwords * 4 + 4, st);
-    cudaMemsetAsync(sl.d_ctr, 0, 16, st);
-    cudaMemsetAsync(sl.d_status, 0, sizeof(int), st);
-    cudaMemsetAsync(sl.d_counts, 0, (2 * nseg + 1) * sizeof(unsigned long long), st);
-    cudaMemsetAsync(sl.d_steps, 0, 4 * sizeof(unsigned long long), st);
+    ck(cudaMemcpyAsync(sl.d_segs, sl.h_segs, nseg * sizeof(Seg), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(sl.d_tiles, sl.h_tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, st));
+    ck(cudaMemsetAsync(sl.d_flags, 0, nwords * 4 + 4, st));
+    ck(cudaMemsetAsync(sl.d_ctr, 0, 16, st));
+    ck(cudaMemsetAsync(sl.d_status, 0, sizeof(int), st));
+    ck(cudaMemsetAsync(sl.d_counts, 0, (2 * nseg + 1) * sizeof(unsigned long long), st));
+    ck(cudaMemsetAsync(sl.d_steps, 0, 4 * sizeof(unsigned long long), st));
     uint64_t dmax = 0;
     for (const Part &p : sl.items) dmax = std::max(dmax, p.d0 + 8 * (p.ncand - 1));
     if (nt > 0) {
@@ -220,8 +231,9 @@ bool launch_batch(eis_server *s, Slot &sl) {
         }
         int nbaby, log2n;
         eis_giant_params(dmax, 0, nbaby, log2n);
-        cudaMemcpyAsync(sl.d_mem_d, sl.h_mem_d, nmem * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(sl.d_mem_ctl, 0, 64, st);
+        ck(cudaMemcpyAsync(sl.d_mem_d, sl.h_mem_d, nmem * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                           st));
+        ck(cudaMemsetAsync(sl.d_mem_ctl, 0, 64, st));
         k_giant<<<std::min<uint32_t>(nmem, s->giant_grid), 32, (size_t)8 << log2n, st>>>(
             sl.d_mem_d, nullptr, 0, nullptr, nullptr, nmem,
             reinterpret_cast<uint32_t *>(sl.d_mem_ctl), cv.d_primes, cv.d_sqtab, cv.nprimes,
@@ -229,13 +241,16 @@ bool launch_batch(eis_server *s, Slot &sl) {
             nullptr, nullptr, reinterpret_cast<unsigned long long *>(sl.d_mem_ctl + 8),
             reinterpret_cast<int *>(sl.d_mem_ctl + 24), nbaby, log2n, 1u << 20, cv.giant_compose,
             nullptr);
-        cudaMemcpyAsync(sl.h_mem_out, sl.d_mem_out, nmem, cudaMemcpyDeviceToHost, st);
+        ck(cudaGetLastError());
+        ck(cudaMemcpyAsync(sl.h_mem_out, sl.d_mem_out, nmem, cudaMemcpyDeviceToHost, st));
     }
-    cudaMemcpyAsync(sl.h_counts, sl.d_counts, 2 * nseg * sizeof(unsigned long long),
-                    cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(sl.done_ev, st);
-    return cudaGetLastError() == cudaSuccess;
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(sl.h_counts, sl.d_counts, 2 * nseg * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(sl.h_ctr, sl.d_ctr, 16, cudaMemcpyDeviceToHost, st));
+    ck(cudaEventRecord(sl.done_ev, st));
+    return ok;
 }
 
 void finish_request(eis_server *s, uint64_t id, Request &r) {
@@ -244,6 +259,25 @@ void finish_request(eis_server *s, uint64_t id, Request &r) {
     if (r.status == EIS_OK && r.kind == EIS_REQ_MEMBER && r.sumD == 0) r.status = EIS_ENOTD;
     s->st.requests_done++;
     (void)id;
+}
+
+// A batch that could not be launched: every request part it held completes
+// with EIS_EDEVICE (its counts were never written), and the slot is left
+// idle.  Called with s->mu held.
+void fail_batch(eis_server *s, Slot &sl) {
+    for (const std::vector<Part> *v : {&sl.items, &sl.members}) {
+        for (const Part &p : *v) {
+            auto it = s->reqs.find(p.req);
+            if (it == s->reqs.end()) continue;
+            Request &r = it->second;
+            if (r.status == EIS_OK) r.status = EIS_EDEVICE;
+            if (--r.parts_left == 0) finish_request(s, it->first, r);
+        }
+    }
+    sl.items.clear();
+    sl.members.clear();
+    sl.busy = false;
+    s->failed = true;
 }
 
 void dispatcher(eis_server *s) {
@@ -259,6 +293,8 @@ void dispatcher(eis_server *s) {
             const int bstatus = (q != cudaSuccess) ? EIS_EDEVICE
                                 : ((*sl.h_status & (kErrSteps | kErrGiant)) ? EIS_ESTEPS : EIS_OK);
             if (q != cudaSuccess) s->failed = true;
+            if (q == cudaSuccess && s->defer_after && !sl.items.empty())
+                s->st.deferred += std::min(sl.h_ctr[2], s->defer_cap);
             for (size_t i = 0; i < sl.items.size(); ++i) {
                 auto it = s->reqs.find(sl.items[i].req);
                 if (it == s->reqs.end()) continue;
@@ -334,12 +370,14 @@ void dispatcher(eis_server *s) {
                 s->st.max_batch_parts = std::max<uint64_t>(s->st.max_batch_parts,
                                                            sl.items.size() + sl.members.size());
             }
+            progressed = true;
             if (!launch_batch(s, sl)) {
                 std::lock_guard<std::mutex> lk(s->mu);
-                s->failed = true;
+                fail_batch(s, sl);
+                s->cv_done.notify_all();
+                continue;
             }
             sl.busy = true;
-            progressed = true;
         }
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -387,6 +425,7 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
         if (cfg->max_pending) c.max_pending = cfg->max_pending;
         c.giant_after = cfg->giant_after;
         c.giant_max = cfg->giant_max;
+        c.fail_launches = cfg->fail_launches;
     }
     if (c.giant_after == 0) c.giant_after = 131072;
     if (c.slots > 64 || c.slot_candidates < 64 || c.slot_candidates > ((uint64_t)1 << 30) ||
@@ -402,6 +441,7 @@ int eis_server_create(eis_ctx *ctx, const eis_server_config *cfg, eis_server **o
     s->grid = v.walk_grid;
     s->giant_grid = v.giant_grid;
     s->defer_after = c.giant_after == 0xffffffffu ? 0u : c.giant_after;
+    s->fail_left = c.fail_launches;
     s->step_limit = v.step_limit;
     // At most giant_max walks of a batch go to the giant-step kernel (default:
     // an eighth of a slot, in practice every walk past giant_after; capping

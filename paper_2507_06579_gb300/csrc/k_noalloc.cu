@@ -1,11 +1,15 @@
 // k_noalloc.cu -- eis_classify_range_noalloc: classification without any
 // device allocation.
 //
-// Who needs this: code that runs where cudaMalloc is not allowed or not
-// safe to call -- inside a host callback or a custom allocator hook, in a
-// process whose memory is owned by another framework's pool, or in a
-// real-time loop that forbids allocation after start-up.  eis_create itself
-// allocates (prime table, stream), so such callers cannot hold a context.
+// Who needs this: code that must not allocate device memory -- a custom
+// allocator hook (calling cudaMalloc from inside it would recurse into the
+// allocator it implements), a process whose GPU memory is owned by another
+// framework's pool (a cudaMalloc behind the pool's back can fail or break its
+// accounting), or a real-time loop that forbids allocation after start-up.
+// eis_create itself allocates (prime table, stream), so such callers cannot
+// hold a context.  This call does make CUDA runtime calls (memsets, launches,
+// one copy and a stream synchronisation), so it is not for host functions
+// enqueued with cudaLaunchHostFunc, where CUDA calls are not allowed.
 //
 // The scratch the pipeline needs (survivor queue, tile counts, counters and,
 // when the caller does not want it, the square-free bitmap) lives in one
@@ -88,10 +92,16 @@ __global__ void __launch_bounds__(256) k_na_sieve(uint64_t d0, uint32_t ncand,
 }
 
 // Prefix of at most 16 tile counts, then the survivor queue (variant of
-// k_scan_tiles + k_compact for one interval).
+// k_scan_tiles + k_compact for one interval).  As in k_compact, the tile is
+// taken in chunks of 256 bitmap words, one per thread; a block scan of the
+// words' popcounts places each word's survivors in a shared-memory stage,
+// which the block copies to the queue with consecutive threads writing
+// consecutive entries.
 __global__ void __launch_bounds__(256) k_na_compact(uint32_t ncand, uint32_t ntiles,
                                                     const uint32_t *__restrict__ sqfree) {
-    __shared__ uint32_t base_s, wsum[8];
+    __shared__ uint32_t red[32];
+    __shared__ uint32_t stage[256 * 32];  // one chunk: at most 8192 survivors
+    __shared__ uint32_t base_s;
     const uint32_t t = blockIdx.x;
     const uint32_t *pop = reinterpret_cast<const uint32_t *>(g_na_scratch + kOffTilePop);
     if (threadIdx.x == 0) {
@@ -103,39 +113,26 @@ __global__ void __launch_bounds__(256) k_na_compact(uint32_t ncand, uint32_t nti
             ctr[0] = b + pop[t];
         }
     }
+    __syncthreads();
+    uint32_t out = base_s;
     const uint32_t c0 = t * kTileCands;
     const uint32_t nc = min((uint32_t)kTileCands, ncand - c0);
     const uint32_t nw = (nc + 31) >> 5;
-    constexpr uint32_t kPer = kTileWords / 256;
-    uint32_t v[kPer], cnt = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        const uint32_t w = threadIdx.x * kPer + k;
-        v[k] = (w < nw) ? sqfree[(c0 >> 5) + w] : 0u;
-        cnt += __popc(v[k]);
-    }
-    // exclusive scan of cnt over the block
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= (uint32_t)o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    uint32_t before = 0;
-    for (uint32_t i = 0; i < wid; ++i) before += wsum[i];
-    uint32_t out = base_s + before + x - cnt;
     uint32_t *queue = reinterpret_cast<uint32_t *>(g_na_scratch + kOffQueue);
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        uint32_t bitsv = v[k];
-        const uint32_t cb = c0 + 32u * (threadIdx.x * kPer + k);
-        while (bitsv) {
-            const int b = __ffs(bitsv) - 1;
-            queue[out++] = cb + (uint32_t)b;
-            bitsv &= bitsv - 1;
+    for (uint32_t w0 = 0; w0 < nw; w0 += 256) {
+        const uint32_t w = w0 + threadIdx.x;
+        uint32_t x = (w < nw) ? sqfree[(c0 >> 5) + w] : 0u;
+        uint32_t tot;
+        uint32_t o = block_excl_scan((uint32_t)__popc(x), red, &tot);
+        const uint32_t cb = c0 + 32u * w;
+        while (x) {
+            stage[o++] = cb + (uint32_t)(__ffs(x) - 1);
+            x &= x - 1;
         }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tot; i += 256) queue[out + i] = stage[i];
+        out += tot;
+        __syncthreads();
     }
 }
 
@@ -171,20 +168,42 @@ int na_setup(int device) {
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (g_na_ready[device]) return EIS_OK;
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr) {
-        cudaGetLastError();
-        return EIS_EDEVICE;
-    }
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr) return EIS_EDEVICE;
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_persistent, 256, 0) != cudaSuccess) {
-        cudaGetLastError();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_persistent, 256, 0) != cudaSuccess)
         return EIS_EDEVICE;
-    }
     g_na_ptr[device] = static_cast<unsigned char *>(p);
     g_na_grid[device] = sms * (occ > 0 ? occ : 1);
     g_na_ready[device] = true;
     return EIS_OK;
+}
+
+// Makes `device` current for the call and gives the caller's device back on
+// every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == device) || cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Launch with the launch's own status as the return value, so the call never
+// reads (and clears) an error left pending by the caller's earlier work.
+template <class... Params, class... Args>
+cudaError_t launch(void (*kernel)(Params...), uint32_t grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 }  // namespace
@@ -199,10 +218,8 @@ extern "C" int eis_classify_range_noalloc(int device, uint64_t lo, uint64_t hi, 
     const uint64_t d0 = lo + ((13 - lo % 8) % 8);
     const uint64_t n = hi > d0 ? (hi - d0 + 7) / 8 : 0;
     if (n > kNaMaxCands) return EIS_ETOOLARGE;
-    if (cudaSetDevice(device) != cudaSuccess) {
-        cudaGetLastError();
-        return EIS_EDEVICE;
-    }
+    DeviceGuard guard(device);
+    if (!guard.ok) return EIS_EDEVICE;
     int rc = na_setup(device);
     if (rc != EIS_OK) return rc;
     if (n == 0) {
@@ -219,25 +236,24 @@ extern "C" int eis_classify_range_noalloc(int device, uint64_t lo, uint64_t hi, 
     // The array keeps the previous call's contents: clear the counters and
     // the caller's flag words, which the walk only ORs into.
     if (cudaMemsetAsync(base + kOffCounters, 0, 64, s) != cudaSuccess ||
-        cudaMemsetAsync(flags_out, 0, (size_t)nwords * 4, s) != cudaSuccess) {
-        cudaGetLastError();
+        cudaMemsetAsync(flags_out, 0, (size_t)nwords * 4, s) != cudaSuccess)
         return EIS_EDEVICE;
-    }
-    k_na_sieve<<<ntiles, 256, 0, s>>>(d0, ncand, sq);
-    k_na_compact<<<ntiles, 256, 0, s>>>(ncand, ntiles, sq);
-    k_walk_persistent<<<g_na_grid[device], 256, 0, s>>>(
-        reinterpret_cast<const Seg *>(base + kOffSeg), 1u,
-        reinterpret_cast<const uint32_t *>(base + kOffQueue), ctr, ctr + 1, flags_out, nullptr,
-        c64, reinterpret_cast<int *>(ctr + 2), 1u << 26, 0u, nullptr, nullptr, 0u,
-        d0 + 8 * (n - 1) < kFastDLimit ? 1 : 0);
-    k_na_count<<<(nwords + 255) / 256 < 304 ? (nwords + 255) / 256 : 304, 256, 0, s>>>(nwords, flags_out, sq);
-    if (cudaGetLastError() != cudaSuccess) return EIS_EDEVICE;
+    const uint32_t count_grid = (nwords + 255) / 256 < 304 ? (nwords + 255) / 256 : 304;
+    if (launch(k_na_sieve, ntiles, s, d0, ncand, sq) != cudaSuccess ||
+        launch(k_na_compact, ntiles, s, ncand, ntiles, (const uint32_t *)sq) != cudaSuccess ||
+        launch(k_walk_persistent, (uint32_t)g_na_grid[device], s,
+               reinterpret_cast<const Seg *>(base + kOffSeg), 1u,
+               reinterpret_cast<const uint32_t *>(base + kOffQueue), (const uint32_t *)ctr,
+               ctr + 1, flags_out, (uint8_t *)nullptr, c64, reinterpret_cast<int *>(ctr + 2),
+               1u << 26, 0u, (uint32_t *)nullptr, (uint32_t *)nullptr, 0u,
+               d0 + 8 * (n - 1) < kFastDLimit ? 1 : 0) != cudaSuccess ||
+        launch(k_na_count, count_grid, s, nwords, (const uint32_t *)flags_out,
+               (const uint32_t *)sq) != cudaSuccess)
+        return EIS_EDEVICE;
     unsigned long long host[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(host, base + kOffCounters, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
+        cudaStreamSynchronize(s) != cudaSuccess)
         return EIS_EDEVICE;
-    }
     // host[0]: survivors | queue head, host[1]: status, host[2]: steps, host[3]: #E
     int status = 0;
     std::memcpy(&status, &host[1], sizeof(int));

@@ -1,10 +1,13 @@
 """Serving: continuous batching of range-count and membership requests.
 
 The bar is exact: every result must be the same when the request runs alone
-and when it runs mixed with others (counts are integers).  Failure handling is
-exercised on the host only: a full queue refuses submits (EIS_EBUSY), a wait
-can time out, a queued request can be cancelled, and a step-limit error in a
-batch reaches its requests as EIS_ESTEPS.
+and when it runs mixed with others (counts are integers), and equal to the
+CPU oracle's, also when long walks inside a batch are handed to the
+giant-step kernel.  Failure handling is exercised on the host only: a full
+queue refuses submits (EIS_EBUSY), a wait can time out, a queued request can
+be cancelled, a step-limit error in a batch reaches its requests as
+EIS_ESTEPS, and a batch launch that fails (faked before anything is
+enqueued) fails its requests with EIS_EDEVICE.
 """
 import numpy as np
 import pytest
@@ -146,3 +149,54 @@ def test_server_memory_admission():
             rid = srv.submit_count(5, 10**6 + 1)
             rc, res, _ = srv.wait(rid)
             assert rc == E.EIS_OK and res == c.count_range(5, 10**6 + 1)
+
+
+def _oracle_answer(orc, kind, lo, hi):
+    """(status, result) the server must return, from the CPU oracle."""
+    if kind == "count":
+        _, nE, _ = orc.count_range(lo, hi)
+        return E.EIS_OK, nE
+    rc, theta, _ = orc.walk_mod2(lo)
+    if rc == orc.ORC_ENOTD:
+        return E.EIS_ENOTD, 0
+    assert rc == 0
+    return E.EIS_OK, int(theta == 1)
+
+
+@pytest.mark.parametrize("giant_after", [600, 0xffffffff], ids=["giant_handover", "walk_only"])
+def test_server_results_match_oracle(ctx, orc, giant_after):
+    """Every answer of a seeded mixed stream (range counts and membership
+    queries) equals the oracle's.  With giant_after = 600 most range walks
+    pass 600 baby steps inside a batch and are handed to the giant-step
+    kernel (checked through the server's deferred counter); with 0xffffffff
+    none is, and the same answers come from the baby walk alone."""
+    reqs = W.serving_stream(200, 1e3, seed=41, len_range=(1e2, 2e4), d_max=1e10,
+                            a_range=(1e6, 1e10))
+    want = [_oracle_answer(orc, k, lo, hi) for _, k, lo, hi in reqs]
+    with E.Server(ctx, slots=3, giant_after=giant_after, giant_max=1 << 16) as srv:
+        ids = [srv.submit_member(lo) if k == "member" else srv.submit_count(lo, hi)
+               for _, k, lo, hi in reqs]
+        got = [srv.wait(i)[:2] for i in ids]
+        st = srv.stats()
+    for (rc, res), (rc_o, res_o), r in zip(got, want, reqs):
+        assert rc == rc_o, r
+        if rc == E.EIS_OK:
+            assert res == res_o, r
+    if giant_after == 600:
+        assert st["deferred"] > 100
+    else:
+        assert st["deferred"] == 0
+
+
+def test_failed_launch_fails_its_requests(ctx):
+    """A batch whose launch fails (faked on the host by the fail_launches
+    hook, before anything is enqueued) completes every request it held, and
+    every request still queued, with EIS_EDEVICE: none returns EIS_OK with
+    counts that were never written.  The context itself stays usable."""
+    with E.Server(ctx, slots=1, fail_launches=1) as srv:
+        ids = [srv.submit_count(10**6 + 1000 * i, 10**6 + 1000 * i + 800) for i in range(12)]
+        ids.append(srv.submit_member(1901))
+        rcs = [srv.wait(i)[0] for i in ids]
+    assert all(rc == E.EIS_EDEVICE for rc in rcs), rcs
+    assert ctx.count_range(10**6, 10**6 + 800) == ctx.count_range(10**6, 10**6 + 800)
+    assert ctx.is_eisenstein(1901) is True

@@ -1,12 +1,13 @@
 """The no-allocation entry point eis_classify_range_noalloc.
 
-It is for callers that may not allocate device memory (code inside host
-callbacks or allocator hooks, processes whose GPU memory belongs to another
+It is for callers that may not allocate device memory (allocator hooks, which
+would recurse into themselves, processes whose GPU memory belongs to another
 framework's pool, loops that forbid allocation after start-up).  Its scratch
 is a fixed array inside the library, shared by every call.  The test calls it
 through the C-ABI twice in a row -- first the largest range it accepts, then
 a smaller one, so stale scratch from the first call would show up in the
-second -- and compares both with eis_classify_range bit for bit.  It runs
+second -- and compares both with eis_classify_range bit for bit.  A third
+test compares its output with the CPU oracle candidate by candidate.  It runs
 alone or after the rest of the suite (this file is collected last).
 """
 import ctypes
@@ -59,6 +60,26 @@ def test_noalloc_matches_classify_range_twice():
         lo, hi = cases[1]
         rc, f, _, c = _call(torch, lo, hi, with_sqfree=False)
         assert rc == E.EIS_OK and c == refs[1][2] and np.array_equal(f, refs[1][0])
+
+
+def _unpack(words, n):
+    return np.unpackbits(words.view(np.uint8), bitorder="little")[:n]
+
+
+def test_noalloc_matches_oracle():
+    """10^5 candidates near 10^7 (several sieve tiles and a ragged last word),
+    each code (not in D / D minus E / E) equal to the oracle's."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    E.build()
+    lo, hi = _range_with(100_001, 10**7)
+    rc, f, s, c = _call(torch, lo, hi)
+    assert rc == E.EIS_OK, E.lib().eis_strerror(rc)
+    n, _ = E.num_candidates(lo, hi)
+    codes = np.where(_unpack(f, n) == 1, 2, _unpack(s, n)).astype(np.uint8)
+    ref = oracle.classify_range(lo, hi)["codes"]
+    assert np.array_equal(codes, ref)
+    assert c == int((ref == 2).sum())
 
 
 def test_noalloc_allocates_nothing_after_setup():
