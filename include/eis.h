@@ -82,6 +82,24 @@ extern "C" {
                                  /* budget in bytes                           */
 #define EIS_OPT_MEM_IN_USE 10    /* read-only: bytes charged to the budget    */
                                  /* (context tables, live plans and servers)  */
+#define EIS_OPT_GIANT_KERNEL 11  /* which search takes walks past the          */
+                                 /* threshold: EIS_GIANT_* (EIS_GIANT_LANE)    */
+#define EIS_OPT_MARK_EVERY 12    /* lane search: about 1 state in this many is */
+                                 /* marked and kept in the baby table (16)     */
+#define EIS_OPT_BSGS_CHUNK 13    /* lane search: survivors per round of record */
+                                 /* walk + search (2^21); sizes the table pool */
+#define EIS_OPT_BSGS_WALK_CAP 14 /* lane search: steps a giant cycle may walk  */
+                                 /* without meeting a marked state before its  */
+                                 /* d is finished by the plain walk (2^14)     */
+
+/* Giant-step searches of plans (EIS_OPT_GIANT_KERNEL).  Both run after
+ * EIS_OPT_GIANT_THRESHOLD baby steps without a centre. */
+#define EIS_GIANT_LANE 0 /* one d per lane: the baby walk keeps the marked states  */
+                         /* (Q < 1.39/mark_every * floor(sqrt d)) in a table, and   */
+                         /* each giant cycle walks to a marked state and looks it  */
+                         /* up (plans of >= 2^18 candidates; smaller plans walk)   */
+#define EIS_GIANT_WARP 1 /* one d per warp: the full baby table in shared memory  */
+                         /* (the single-query kernel)                              */
 
 /* Giant-step compositions (EIS_OPT_GIANT_COMPOSE). */
 #define EIS_COMPOSE_TEXTBOOK 0 /* product of forms, then rho until reduced      */

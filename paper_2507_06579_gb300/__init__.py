@@ -65,6 +65,12 @@ EIS_OPT_GIANT_STRIDE = 7
 EIS_OPT_GIANT_COMPOSE = 8
 EIS_OPT_MEM_BUDGET = 9
 EIS_OPT_MEM_IN_USE = 10
+EIS_OPT_GIANT_KERNEL = 11
+EIS_OPT_MARK_EVERY = 12
+EIS_OPT_BSGS_CHUNK = 13
+EIS_OPT_BSGS_WALK_CAP = 14
+EIS_GIANT_LANE = 0
+EIS_GIANT_WARP = 1
 EIS_COMPOSE_TEXTBOOK = 0
 EIS_COMPOSE_NUCOMP = 1
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "eis.h"
+#include "eis_bsgs.cuh"
 #include "eis_internal.h"
 #include "eis_kernels.h"
 
@@ -53,7 +54,13 @@ struct eis_ctx {
     int64_t giant_threshold = 0;
     int64_t giant_stride = 0;
     int giant_compose = EIS_COMPOSE_TEXTBOOK;
+    int giant_kernel = EIS_GIANT_LANE;
+    int mark_every = 16;                    // marked states: about 1 in mark_every
+    int64_t bsgs_chunk = (int64_t)1 << 21;  // survivors per record/search round
+    int64_t bsgs_walk_cap = 1 << 14;        // steps a giant cycle's walk may take
     int occ_persistent = 1;
+    int occ_record = 1;                     // resident CTAs/SM of k_walk_record
+    int occ_bsgs = 1;                       // ... and of k_bsgs
     eis_stats last{};
 };
 
@@ -88,6 +95,19 @@ struct eis_plan {
     int fast = 1;                 // every d of the plan is below kFastDLimit
     int giant_nbaby = 0, giant_log2n = 0;
     uint32_t giant_grid = 0;
+    // lane-per-d search (EIS_GIANT_LANE): the survivor queue in rounds of
+    // bsgs_chunk positions; each round runs the recording walk, the table
+    // index, the search and the fallback walk
+    int bsgs = 0;
+    uint32_t bsgs_nbaby = 0, bsgs_chunk = 0, bsgs_rounds = 0;
+    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0;
+    float bsgs_tau = 0.0f;
+    DRecord *d_recs = nullptr;
+    unsigned char *d_pool = nullptr;
+    uint32_t *d_fb = nullptr;
+    uint32_t *d_bctr = nullptr;  // [0] walk head [1] records [2] pool head [3] search head
+                                 // [4] fallbacks [5] fallback walk head
+    std::vector<cudaEvent_t> bev;  // per round: start, after the walk, end
     uint64_t bytes = 0;
     uint32_t walk_grid = 0;
     int launches = 0;
@@ -178,6 +198,10 @@ static void giant_params(uint64_t d, int64_t forced, int &nbaby, int &log2n) {
 static constexpr int kGiantMaxLog2 = 14;  // 128 KB table per warp at most
 static constexpr uint32_t kGiantMaxRounds = 1u << 20;
 static constexpr double kTuneMargin = 0.98;  // autotuner: keep the current setting unless 2% faster
+static constexpr uint32_t kBsgsMaxCycles = 1u << 20;  // giant cycles per d before the fallback walk
+// Plans with fewer candidates than this walk every d to its centre (the
+// search's table pool is not worth allocating for them).
+static constexpr uint64_t kBsgsMinCands = (uint64_t)1 << 18;
 
 static void record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
     if (capturing)
@@ -209,11 +233,40 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
             k_compact<<<ntiles, 256, 0, s>>>(p->d_tiles, p->d_sqfree, p->d_tile_off, p->d_surv);
             launches += 2;
             record(p->ev[1], s, capturing);
-            k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
-                p->d_segs, nseg, p->d_surv, p->d_ctr, p->d_ctr + 1, p->d_flags, p->d_glog,
-                p->d_steps, p->d_status, limit, p->defer_after, p->d_defer, p->d_ctr + 2,
-                p->defer_cap, p->fast);
-            ++launches;
+            if (p->bsgs) {
+                const uint32_t C = p->bsgs_chunk;
+                for (uint32_t r = 0; r < p->bsgs_rounds; ++r) {
+                    const uint32_t q_lo = r * C;
+                    const uint32_t q_hi = (uint32_t)std::min<uint64_t>((uint64_t)q_lo + C, 0xffffffffull);
+                    record(p->bev[3 * r], s, capturing);
+                    EIS_CK(cudaMemsetAsync(p->d_bctr, 0, 8 * sizeof(uint32_t), s));
+                    k_walk_record<<<p->bsgs_grid_a, 256, 0, s>>>(
+                        p->d_segs, nseg, p->d_surv, p->d_ctr, q_lo, q_hi, p->d_bctr,
+                        p->d_flags, p->d_glog, p->d_steps, p->d_status, limit, p->bsgs_nbaby,
+                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_bctr + 2,
+                        p->fast);
+                    record(p->bev[3 * r + 1], s, capturing);
+                    k_bsgs_index<<<(C + 127) / 128, 128, 0, s>>>(p->d_recs, p->d_bctr + 1, C,
+                                                                  p->d_pool, p->d_steps + 3);
+                    k_bsgs<<<p->bsgs_grid_b, 128, 0, s>>>(
+                        p->d_segs, nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
+                        p->d_flags, p->d_glog, p->d_steps + 1, p->d_status, p->d_fb,
+                        p->d_bctr + 4, C, p->bsgs_tau, c->giant_compose, kBsgsMaxCycles,
+                        p->bsgs_walk_cap, p->fast);
+                    k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
+                        p->d_segs, nseg, p->d_fb, p->d_bctr + 4, p->d_bctr + 5, p->d_flags,
+                        p->d_glog, p->d_steps, p->d_status, limit, 0u, nullptr, nullptr, 0u,
+                        p->fast);
+                    record(p->bev[3 * r + 2], s, capturing);
+                    launches += 4;
+                }
+            } else {
+                k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
+                    p->d_segs, nseg, p->d_surv, p->d_ctr, p->d_ctr + 1, p->d_flags, p->d_glog,
+                    p->d_steps, p->d_status, limit, p->defer_after, p->d_defer, p->d_ctr + 2,
+                    p->defer_cap, p->fast);
+                ++launches;
+            }
             record(p->ev[2], s, capturing);
             if (p->d_defer) {
                 const size_t smem = (size_t)8 << p->giant_log2n;
@@ -257,9 +310,11 @@ static void plan_free(eis_plan *p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : p->bev)
+        if (e) cudaEventDestroy(e);
     void *bufs[] = {p->d_segs, p->d_tiles, p->d_sqfree, p->d_flags, p->d_tile_pop, p->d_tile_off,
                     p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog,
-                    p->d_defer, p->d_cls};
+                    p->d_defer, p->d_cls, p->d_recs, p->d_pool, p->d_fb, p->d_bctr};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->ctx) ctx_release(p->ctx, p->bytes);
@@ -343,7 +398,37 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     EIS_ALLOC(p->d_steps, 4 * sizeof(unsigned long long));
     if (with_log) EIS_ALLOC(p->d_glog, p->total_cand);
     if (flags & EIS_PLAN_CLASSES) EIS_ALLOC(p->d_cls, 3 * nseg * sizeof(unsigned long long) + 8);
-    if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && p->total_cand > 0) {
+    if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && c->giant_kernel == EIS_GIANT_LANE &&
+        p->total_cand >= kBsgsMinCands) {
+        // lane-per-d search: survivors in rounds of C queue positions; the
+        // pool holds one table region per resident lane plus one per d a
+        // round can hand on
+        // round, smaller when the budget left cannot hold the default round;
+        // without room for 2^16 survivors per round the plan walks instead
+        const uint64_t lanes = (uint64_t)c->sm_count * c->occ_record * 256;
+        const uint64_t per_d = kBsgsRegionBytes + sizeof(DRecord) + 4;
+        const uint64_t used = c->in_use.load();
+        const uint64_t left = c->budget > used ? c->budget - used : 0;
+        const uint64_t fit = left / per_d > lanes + 64 ? left / per_d - lanes - 64 : 0;
+        uint64_t C = std::min<uint64_t>((uint64_t)c->bsgs_chunk, (p->total_cand + 31) / 32 * 32);
+        C = std::min<uint64_t>(C, fit / 32 * 32);
+        if (C >= ((uint64_t)1 << 16) || C >= (p->total_cand + 31) / 32 * 32) {
+            p->bsgs = 1;
+            p->bsgs_nbaby = (uint32_t)std::min<int64_t>(c->giant_threshold, 0xffffffffll);
+            p->bsgs_tau = 1.39f / (float)c->mark_every;
+            p->bsgs_walk_cap = (uint32_t)c->bsgs_walk_cap;
+            p->bsgs_chunk = (uint32_t)C;
+            p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
+            p->bsgs_grid_a = (uint32_t)(c->sm_count * c->occ_record);
+            p->bsgs_grid_b = (uint32_t)(c->sm_count * c->occ_bsgs);
+            EIS_ALLOC(p->d_pool, (lanes + C) * kBsgsRegionBytes);
+            EIS_ALLOC(p->d_recs, C * sizeof(DRecord));
+            EIS_ALLOC(p->d_fb, C * 4);
+            EIS_ALLOC(p->d_bctr, 8 * sizeof(uint32_t));
+            p->bev.assign(3 * (size_t)p->bsgs_rounds, nullptr);
+        }
+    } else if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 &&
+               c->giant_kernel == EIS_GIANT_WARP && p->total_cand > 0) {
         uint64_t dmax = 0;
         for (const Seg &sg : p->segs)
             if (sg.ncand) dmax = std::max(dmax, sg.d0 + 8 * (sg.ncand - 1));
@@ -362,6 +447,12 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     }
 #undef EIS_ALLOC
     for (auto &e : p->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            plan_free(p);
+            return EIS_EDEVICE;
+        }
+    }
+    for (auto &e : p->bev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
             plan_free(p);
             return EIS_EDEVICE;
@@ -444,11 +535,28 @@ static int plan_fill_stats(eis_plan *p, eis_stats *st) {
     uint32_t ctr[4] = {0, 0, 0, 0};
     EIS_CK(cudaMemcpy(ctr, p->d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
     st->deferred = p->d_defer ? std::min(ctr[2], p->defer_cap) : 0;
+    if (p->bsgs) {
+        // steps[0]: baby steps of the recording and fallback walks, [1]: steps
+        // of the search's walks, [2]: giant cycles, [3]: d handed on
+        st->baby_steps = steps[0] + steps[1];
+        st->giant_steps = steps[2];
+        st->deferred = steps[3];
+    }
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[3]) == cudaSuccess) st->ms_total = ms;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) st->ms_sieve = ms;
     if (cudaEventElapsedTime(&ms, p->ev[1], p->ev[2]) == cudaSuccess) st->ms_walk = ms;
     if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[4]) == cudaSuccess) st->ms_giant = ms;
+    if (p->bsgs) {
+        double walk = 0, giant = 0;
+        for (uint32_t r = 0; r < p->bsgs_rounds; ++r) {
+            if (cudaEventElapsedTime(&ms, p->bev[3 * r], p->bev[3 * r + 1]) == cudaSuccess) walk += ms;
+            if (cudaEventElapsedTime(&ms, p->bev[3 * r + 1], p->bev[3 * r + 2]) == cudaSuccess)
+                giant += ms;
+        }
+        st->ms_walk = walk;
+        st->ms_giant = giant;
+    }
     cudaGetLastError();
     st->launches = p->launches;
     st->sm_count = p->ctx->sm_count;
@@ -626,6 +734,14 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_persistent, 256, 0) != cudaSuccess)
         occ = 1;
     c->occ_persistent = std::max(1, occ);
+    occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk_record, 256, 0) != cudaSuccess)
+        occ = 1;
+    c->occ_record = std::max(1, occ);
+    occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bsgs, 128, 0) != cudaSuccess) occ = 1;
+    c->occ_bsgs = std::max(1, occ);
+    cudaGetLastError();
     *out = c;
     return EIS_OK;
 }
@@ -677,6 +793,22 @@ int eis_set_option(eis_ctx *c, int key, int64_t v) {
             if (v != EIS_COMPOSE_TEXTBOOK && v != EIS_COMPOSE_NUCOMP) return EIS_EINVAL;
             c->giant_compose = (int)v;
             return EIS_OK;
+        case EIS_OPT_GIANT_KERNEL:
+            if (v != EIS_GIANT_LANE && v != EIS_GIANT_WARP) return EIS_EINVAL;
+            c->giant_kernel = (int)v;
+            return EIS_OK;
+        case EIS_OPT_MARK_EVERY:
+            if (v < 2 || v > 4096) return EIS_EINVAL;
+            c->mark_every = (int)v;
+            return EIS_OK;
+        case EIS_OPT_BSGS_CHUNK:
+            if (v < 4096 || v > ((int64_t)1 << 28)) return EIS_EINVAL;
+            c->bsgs_chunk = v;
+            return EIS_OK;
+        case EIS_OPT_BSGS_WALK_CAP:
+            if (v < 1 || v > ((int64_t)1 << 24)) return EIS_EINVAL;
+            c->bsgs_walk_cap = v;
+            return EIS_OK;
         default:
             return EIS_EINVAL;
     }
@@ -693,6 +825,10 @@ int eis_get_option(eis_ctx *c, int key, int64_t *v) {
         case EIS_OPT_GIANT_THRESHOLD: *v = c->giant_threshold; return EIS_OK;
         case EIS_OPT_GIANT_STRIDE: *v = c->giant_stride; return EIS_OK;
         case EIS_OPT_GIANT_COMPOSE: *v = c->giant_compose; return EIS_OK;
+        case EIS_OPT_GIANT_KERNEL: *v = c->giant_kernel; return EIS_OK;
+        case EIS_OPT_MARK_EVERY: *v = c->mark_every; return EIS_OK;
+        case EIS_OPT_BSGS_CHUNK: *v = c->bsgs_chunk; return EIS_OK;
+        case EIS_OPT_BSGS_WALK_CAP: *v = c->bsgs_walk_cap; return EIS_OK;
         case EIS_OPT_MEM_BUDGET: *v = (int64_t)c->budget; return EIS_OK;
         case EIS_OPT_MEM_IN_USE: *v = (int64_t)c->in_use.load(); return EIS_OK;
         default: return EIS_EINVAL;
