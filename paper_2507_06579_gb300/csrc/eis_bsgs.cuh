@@ -65,7 +65,7 @@ struct DRecord {
     uint32_t cand;    // candidate index in the plan layout
     uint32_t k;       // entries in the table (entry k-1 is G = a_jl)
     uint32_t region;  // table region index in the pool
-    uint32_t pad;
+    uint32_t s;       // floor(sqrt d)
 };
 
 EIS_HD uint32_t float_bits(float f) {
@@ -118,11 +118,159 @@ EIS_HD int bsgs_find(const DEntry *e, const uint8_t *slots, uint32_t q, uint32_t
     return -1;
 }
 
+
+// ------------------------------------------------------------ lean product
+// reduce(mu * G) for the search, with every operand of a reduced ideal below
+// 2^23 (d < 2^44): the composition of forms (Cohen, "A Course in Computational
+// Algebraic Number Theory", Algorithm 5.4.7, with f1 = mu and f2 = G fixed, so
+// that c2 = c_G = (b_G^2 - d) / (4 a_G) is computed once per d), its two
+// extended Euclid steps in fp32 (every remainder, quotient and cofactor is an
+// integer below 2^23, so each operation is exact; quotients come from a
+// reciprocal estimate with one correction each way), and the residues mod
+// v1 < 2^22 by a float quotient estimate with integer corrections.
+
+// floor(x / y) for integers 0 <= x < 2^23, 0 < y < 2^23 held in floats, and
+// the remainder.
+EIS_HD float fdivmod(float x, float y, float &rem) {
+#ifdef __CUDA_ARCH__
+    const float e = __fmaf_rd(x, rcp_approx(y), 8388608.0f) - 8388608.0f;
+#else
+    const float e = std::floor(x * (1.0f / y));
+#endif
+    // x rcp(y) lies within (x/y) 2^-22 <= 2 of x/y: at most two corrections
+    float q = e;
+    float r = x - q * y;  // exact: |q y| <= x + 2y < 2^24
+    while (r < 0.0f) {
+        q -= 1.0f;
+        r += y;
+    }
+    while (r >= y) {
+        q += 1.0f;
+        r -= y;
+    }
+    rem = r;
+    return q;
+}
+
+// Extended Euclid on 0 <= A, 0 < B < 2^23 in fp32: returns g = gcd(A, B) with
+// xa A + xb B = g.
+EIS_HD float fegcd(float A, float B, float &xa, float &xb) {
+    float r0 = A, r1 = B, a0 = 1.0f, a1 = 0.0f, b0 = 0.0f, b1 = 1.0f;
+    while (r1 != 0.0f) {
+        float rem;
+        const float q = fdivmod(r0, r1, rem);
+        r0 = r1;
+        r1 = rem;
+        const float ta = a0 - q * a1, tb = b0 - q * b1;  // |cofactors| <= B, A: exact
+        a0 = a1;
+        a1 = ta;
+        b0 = b1;
+        b1 = tb;
+    }
+    xa = a0;
+    xb = b0;
+    return r0;
+}
+
+// x mod m in [0, m) for |x| < 2^23, 0 < m < 2^23.
+EIS_HD int32_t fmodp(int32_t x, int32_t m) {
+    float rem;
+    const float ax = (float)(x < 0 ? -x : x);
+    fdivmod(ax, (float)m, rem);
+    const int32_t r = (int32_t)rem;
+    return (x < 0 && r != 0) ? m - r : r;
+}
+
+// a b mod m for 0 <= a, b < m < 2^22.
+EIS_HD int32_t mulmod22(int32_t a, int32_t b, int32_t m) {
+    const int64_t p = (int64_t)a * b;  // < 2^44
+#ifdef __CUDA_ARCH__
+    const float e = __fmul_rn(__fmul_rn((float)a, (float)b), rcp_approx((float)m));
+#else
+    const float e = ((float)a * (float)b) * (1.0f / (float)m);
+#endif
+    // e is within 0.1 + p/m 2^-22 < 1.1 of p/m: the remainder needs at most two
+    // corrections each way
+    int64_t r = p - (int64_t)e * m;
+    while (r < 0) r += m;
+    while (r >= m) r -= m;
+    return (int32_t)r;
+}
+
+// Per-d constant of the lean product: c_G = (b_G^2 - d) / (4 a_G).
+EIS_HD int64_t lean_cG(const Ideal &G, int64_t d) { return (G.b * G.b - d) / (4 * G.a); }
+
+// rho steps until reduced, as ideal_reduce, also returning Q_{-1} of the
+// result; class gained, or -1 past max_steps.
+EIS_HD int lean_reduce(int64_t &P, int64_t &Q, int64_t &Qm, int64_t d, int64_t s, int max_steps) {
+    Qm = exact_quot(d, P, Q);
+    int g = 0;
+    for (int it = 0; !ideal_is_reduced(P, Q, s); ++it) {
+        if (it >= max_steps) return -1;
+        const int64_t q = Q > 0 ? floor_div_fast(P + s, Q) : floor_div_fast(P + s + 1, Q);
+        const int64_t Pn = q * Q - P;
+        const int64_t Qn = Qm + q * (P - Pn);
+        g += 1 + (int)((Pn >> 1) & 1);
+        Qm = Q;
+        P = Pn;
+        Q = Qn;
+    }
+    return g;
+}
+
+// reduce(mu * G) and Q_{-1} of the result; false if the reduction ran away.
+EIS_HD bool lean_mul(const Ideal &mu, const Ideal &G, int64_t cG, int64_t d, int64_t s, Ideal &out,
+                     int64_t &Qm) {
+    const int32_t a1 = (int32_t)mu.a, a2 = (int32_t)G.a;
+    const int32_t b1 = (int32_t)mu.b, b2 = (int32_t)G.b;
+    const int32_t sh = (b1 + b2) / 2, n = b2 - sh;
+    float fu, fv;
+    const int32_t dd = (int32_t)fegcd((float)a2, (float)a1, fu, fv);  // u a2 + v a1 = dd
+    const int32_t y1 = (int32_t)fu;
+    int32_t x2 = 0, y2 = -1, d1 = dd;
+    if (dd > 1) {
+        const int32_t sm = fmodp(sh, dd);
+        if (sm != 0) {
+            float xs, xd;
+            d1 = (int32_t)fegcd((float)sm, (float)dd, xs, xd);  // xs (sh mod dd) + xd dd = d1
+            // with sh = (sh mod dd) + k dd: xs sh + (xd - xs k) dd = d1
+            x2 = (int32_t)xs;
+            y2 = -((int32_t)xd - (int32_t)xs * ((sh - sm) / dd));
+        }
+    }
+    const int32_t v1 = a1 / d1, v2 = a2 / d1;
+    int32_t r = 0;
+    if (v1 > 1) {
+        const int32_t t1 = mulmod22(mulmod22(fmodp(y1, v1), fmodp(y2, v1), v1), fmodp(n, v1), v1);
+        int32_t t2 = 0;
+        if (x2 != 0) {
+            int64_t cm = cG % v1;
+            if (cm < 0) cm += v1;
+            t2 = mulmod22(fmodp(x2, v1), (int32_t)cm, v1);
+        }
+        r = t1 - t2;
+        if (r < 0) r += v1;
+    }
+    int64_t P = (int64_t)b2 + 2 * (int64_t)v2 * r;  // in [0, Q + 2^22)
+    int64_t Q = 2 * (int64_t)v1 * v2;
+    while (P > s) P -= Q;  // the representative in (s - Q, s]: a reduced
+                           // product is recognised as it is
+    const int gr = lean_reduce(P, Q, Qm, d, s, 256);
+    if (gr < 0) return false;
+    out.a = Q / 2;
+    out.b = P;
+    out.g = (mu.g + G.g + gr) % 3;
+    return true;
+}
+
 // mu * G reduced, with Q_{-1} = (d - P^2)/Q of the result (the state before
-// it on the cycle), by the textbook composition (compose = 0) or NUCOMP (1).
-EIS_HD bool bsgs_giant(int compose, const Ideal &mu, const Ideal &G, int64_t d, int64_t s,
-                       int64_t L, Ideal &out, int64_t &Qm) {
-    const bool ok = compose ? ideal_mul_nucomp(mu, G, d, s, L, out) : ideal_mul(mu, G, d, s, out);
+// it on the cycle): the lean product (compose = 0, the textbook composition
+// of forms), NUCOMP (1), or the general textbook code of eis_infra.cuh (2,
+// the reference the tests compare with).  cG = lean_cG(G, d).
+EIS_HD bool bsgs_giant(int compose, const Ideal &mu, const Ideal &G, int64_t cG, int64_t d,
+                       int64_t s, int64_t L, Ideal &out, int64_t &Qm) {
+    if (compose == 0) return lean_mul(mu, G, cG, d, s, out, Qm);
+    const bool ok = compose == 1 ? ideal_mul_nucomp(mu, G, d, s, L, out) : ideal_mul(mu, G, d, s, out);
     if (!ok) return false;
     Qm = exact_quot(d, out.b, 2 * out.a);
     return true;

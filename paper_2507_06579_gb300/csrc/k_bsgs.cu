@@ -16,6 +16,7 @@
 //                 composes from state x + 1.  A d the search cannot finish
 //                 (reduction or walk past its limits) goes to a fallback
 //                 list that the plain persistent walk finishes.
+#include "eis.h"
 #include "eis_bsgs.cuh"
 #include "eis_common.cuh"
 #include "eis_kernels.h"
@@ -194,7 +195,8 @@ __device__ __forceinline__ void walk_record_body(
                         r.cand = cand;
                         r.k = k;
                         r.region = region;
-                        r.pad = 0;
+                        // s = floor(sqrt d) from C = 2s (+1), exactly
+                        r.s = (uint32_t)__fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f);
                         recs[slot] = r;
                         // regions 0 .. grid-1 are the lanes' first ones; the
                         // pool hands out the rest, one per handed-on d
@@ -283,20 +285,20 @@ __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, 
         atomicOr(status, kErrGiant);
 }
 
-template <bool kFast>
+template <bool kFast, int kCompose>
 __device__ __forceinline__ void bsgs_body(
     const Seg *__restrict__ segs, uint32_t nseg, const DRecord *__restrict__ recs,
     const uint32_t *__restrict__ nrec, uint32_t rec_cap, uint32_t *__restrict__ next_ptr,
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
-    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, int compose, uint32_t max_cycles,
+    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
     uint32_t walk_cap) {
     const uint32_t n = min(*nrec, rec_cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     bool active = false, exhausted = false;
     uint32_t cand = 0, cycles = 0;
-    int64_t d = 0, s = 0, L = 0;
+    int64_t d = 0, s = 0, L = 0, cG = 0;
     float T = 0.0f, C = 0.0f;
     const DEntry *tab = nullptr;
     const uint8_t *slots = nullptr;
@@ -316,8 +318,8 @@ __device__ __forceinline__ void bsgs_body(
                     const DRecord rc = recs[idx];
                     cand = rc.cand;
                     d = (int64_t)cand_to_d(segs, nseg, cand);
-                    s = (int64_t)isqrt_u64((uint64_t)d);
-                    L = compose ? (int64_t)isqrt_u64((uint64_t)s) : 0;
+                    s = (int64_t)rc.s;
+                    if (kCompose == 1) L = (int64_t)isqrt_u64((uint64_t)s);
                     C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
                     T = __fmul_rn(tau, __uint2float_rn((uint32_t)s));
                     tab = reinterpret_cast<const DEntry *>(pool + (size_t)rc.region * kBsgsRegionBytes);
@@ -326,6 +328,7 @@ __device__ __forceinline__ void bsgs_body(
                     G.a = (int64_t)__uint_as_float(ge.x) / 2;
                     G.b = (int64_t)__uint_as_float(ge.y) - s;  // floor(P + s (+ 1/2)) - s = P
                     G.g = (int)(ge.z % 3u);
+                    if (kCompose == 0) cG = lean_cG(G, d);
                     mu = G;
                     cycles = 0;
                     active = true;
@@ -337,14 +340,15 @@ __device__ __forceinline__ void bsgs_body(
         Ideal nx{1, 1, 0};
         int64_t Qm = 2;
         if (active) {
-            const bool ok = bsgs_giant(compose, mu, G, d, s, L, nx, Qm) && ++cycles <= max_cycles;
+            const bool ok = bsgs_giant(kCompose, mu, G, cG, d, s, L, nx, Qm) && ++cycles <= max_cycles;
             if (!ok) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
                 active = false;
             }
         }
-        // ---- walk to the first marked state x, and one step beyond
+        // ---- walk to the first marked state x and one step beyond; a lane
+        // stops there (at x + 1) while the others finish their walks
         LeanState w;
         float Cw = C;
         int gc = 0;
@@ -358,44 +362,44 @@ __device__ __forceinline__ void bsgs_body(
         } else {
             lean_park_idle(w, Cw);
         }
-        int phase = active ? 0 : 2;  // 0: before x, 1: at x, 2: at x + 1 (or idle)
-        float Qx = 0.0f, numx = 0.0f, Qx1 = 0.0f, numx1 = 0.0f;
-        int gx = 0, gx1 = 0;
+        bool walking = active, at_x = false;
+        float numx = 0.0f;
         uint32_t walked = 0;
-        while (__any_sync(kFull, phase < 2)) {
+        while (__any_sync(kFull, walking)) {
 #pragma unroll
             for (int i = 0; i < kBsgsGroup; ++i) {
-                lean_step<kFast>(w, Cw);
-                gc += 1 + w.x;
-                const bool at_x1 = phase == 1;
-                const bool at_x = phase == 0 && w.Q < T;
-                Qx1 = at_x1 ? w.Q : Qx1;
-                numx1 = at_x1 ? w.num : numx1;
-                gx1 = at_x1 ? gc : gx1;
-                Qx = at_x ? w.Q : Qx;
-                numx = at_x ? w.num : numx;
-                gx = at_x ? gc : gx;
-                walked += phase < 2;
-                phase = at_x1 ? 2 : (at_x ? 1 : phase);
+                if (walking) {
+                    lean_step<kFast>(w, Cw);
+                    gc += 1 + w.x;
+                    ++walked;
+                    if (at_x) {
+                        walking = false;  // at x + 1
+                    } else if (w.Q < T) {
+                        at_x = true;      // at x
+                        numx = w.num;
+                    }
+                }
             }
             // a walk that meets no marked state within walk_cap steps gives
             // the d up to the fallback walk
-            if (phase < 2 && walked >= walk_cap) {
+            if (walking && walked >= walk_cap) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
                 active = false;
-                phase = 2;
+                walking = false;
             }
         }
         my_walk += walked;
         if (!active) continue;
-        // ---- look x up: direct key (Q_x, P_x), then mirror key (Q_x, P_{x+1})
+        // ---- look x up: direct key (Q_x, P_x), then mirror key (Q_x, P_{x+1});
+        // the lane stands at x + 1, so Q_x = w.Qp and g_x = gc - 1 - x_{x+1}
+        const int gx = gc - 1 - w.x;
         int g = -1;
-        int e = bsgs_find(tab, slots, __float_as_uint(Qx), __float_as_uint(numx));
+        int e = bsgs_find(tab, slots, __float_as_uint(w.Qp), __float_as_uint(numx));
         if (e >= 0) {
             g = (gx - (int)(tab[e].s % 3u) + 3 * 4) % 3;  // x = l + j
         } else {
-            e = bsgs_find(tab, slots, __float_as_uint(Qx), __float_as_uint(numx1));
+            e = bsgs_find(tab, slots, __float_as_uint(w.Qp), __float_as_uint(w.num));
             if (e >= 0) g = (gx + (int)(tab[e].s % 3u)) % 3;  // x = l - j
         }
         if (g >= 0) {
@@ -403,9 +407,9 @@ __device__ __forceinline__ void bsgs_body(
             my_cycles += cycles;
             active = false;
         } else {
-            mu.a = (int64_t)Qx1 / 2;
-            mu.b = (int64_t)numx1 - s;
-            mu.g = gx1 % 3;
+            mu.a = (int64_t)w.Q / 2;
+            mu.b = (int64_t)w.num - s;
+            mu.g = gc % 3;
         }
     }
     warp_add(&acc[0], my_walk);
@@ -421,12 +425,15 @@ __global__ void __launch_bounds__(128) k_bsgs(
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
     uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, int compose, uint32_t max_cycles,
     uint32_t walk_cap, int fast) {
-    if (fast)
-        bsgs_body<true>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc, status,
-                        fb_list, fb_count, fb_cap, tau, compose, max_cycles, walk_cap);
-    else
-        bsgs_body<false>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc, status,
-                         fb_list, fb_count, fb_cap, tau, compose, max_cycles, walk_cap);
+#define EIS_BSGS_BODY(F, K)                                                                     \
+    bsgs_body<F, K>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc, status, \
+                    fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap)
+    if (fast) {
+        if (compose == EIS_COMPOSE_NUCOMP) EIS_BSGS_BODY(true, 1); else EIS_BSGS_BODY(true, 0);
+    } else {
+        if (compose == EIS_COMPOSE_NUCOMP) EIS_BSGS_BODY(false, 1); else EIS_BSGS_BODY(false, 0);
+    }
+#undef EIS_BSGS_BODY
 }
 
 }  // namespace eis

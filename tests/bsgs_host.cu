@@ -4,7 +4,8 @@
 // giant steps (eis_infra.cuh) and the search order are the library's own
 // code.  Reads lines
 //     d N tau compose extra verify
-// and prints one line per d:
+// (compose: 0 the lean product, 1 NUCOMP, 2 the general textbook code) and
+// prints one line per d:
 //     status g babysteps cycles walksteps k jl hit
 // status 0 = centre reached in the baby walk (g = log eps_d), 1 = found by
 // the giant-step search, 2 = fallback (too few marked states: the search
@@ -122,6 +123,7 @@ int main() {
         const DEntry &ge = tab.back();
         const Ideal G{(int64_t)bits_float(ge.q) / 2,
                       (int64_t)bits_float(ge.num) - s, (int)(ge.s % 3)};
+        const int64_t cG = lean_cG(G, d);
         Ideal mu = G;
         int64_t cycles = 0, walked = 0;
         int status = -1, hitok = 0;
@@ -132,7 +134,7 @@ int main() {
         for (; cycles < (1 << 20) && status < 0; ++cycles) {
             Ideal nx;
             int64_t Qm = 0;
-            if (!bsgs_giant((int)compose, mu, G, d, s, L, nx, Qm)) {
+            if (!bsgs_giant((int)compose, mu, G, cG, d, s, L, nx, Qm)) {
                 status = -2;
                 break;
             }

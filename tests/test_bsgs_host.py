@@ -3,7 +3,8 @@ on the host against the oracle.
 
 The host model (bsgs_host.cu) walks baby steps in plain integers and uses
 the library's own table, index, marking threshold and giant steps.  Its
-answers must equal the oracle's log eps_d for every d, in both compositions,
+answers must equal the oracle's log eps_d for every d, with the lean product,
+NUCOMP and the general textbook composition,
 with every giant cycle ending one step after its first marked state (the
 kernel's order), or walking on for a while (as lanes of a warp that wait
 for each other would).  With
@@ -72,7 +73,7 @@ def _check(orc, rows, out, want_verified):
     return searched
 
 
-@pytest.mark.parametrize("compose", [0, 1], ids=["textbook", "nucomp"])
+@pytest.mark.parametrize("compose", [0, 1, 2], ids=["lean", "nucomp", "textbook"])
 def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose):
     """d up to 1e10 (whole periods walkable): every hit at l - j or l + j."""
     rng = np.random.default_rng(71 + compose)
@@ -86,7 +87,7 @@ def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose):
     assert _check(orc, rows, out, True) > len(rows) // 2
 
 
-@pytest.mark.parametrize("compose", [0, 1], ids=["textbook", "nucomp"])
+@pytest.mark.parametrize("compose", [0, 1, 2], ids=["lean", "nucomp", "textbook"])
 def test_search_matches_oracle_near_1e11_1e12_and_2p44(bsgs_host, orc, compose):
     rng = np.random.default_rng(83 + compose)
     rows = []
@@ -104,7 +105,7 @@ def test_a_full_table_ends_the_baby_walk_early(bsgs_host, orc):
     """Dense marks (1 state in 3) fill the 128-entry table after ~380 steps:
     the baby walk stops there and the search still finds every unit."""
     rng = np.random.default_rng(97)
-    rows = [(d, 4096, 1.39 / 3, c, 0, 1) for d in _ds(orc, rng, 10**9, 10**10, 20) for c in (0, 1)]
+    rows = [(d, 4096, 1.39 / 3, c, 0, 1) for d in _ds(orc, rng, 10**9, 10**10, 20) for c in (0, 1, 2)]
     out = _run(bsgs_host, rows)
     assert _check(orc, rows, out, True) > 0
     for (status, g, baby, *_rest), (_, _, _, _, _, _) in zip(out, rows):

@@ -90,9 +90,9 @@ def test_products_land_on_the_cycle_with_their_class(infra_host, orc, lo, hi):
     rows = r.stdout.split("\n")
     n_small = 0
     for (d, i, k, index, dsum), row in zip(expect, rows):
-        okT, aT, bT, gT, okN, aN, bN, gN = map(int, row.split())
-        assert okT == 1 and okN == 1, (d, i, k)
-        for a, b, g in ((aT, bT, gT), (aN, bN, gN)):
+        okT, aT, bT, gT, okN, aN, bN, gN, okL, aL, bL, gL = map(int, row.split())
+        assert okT == 1 and okN == 1 and okL == 1, (d, i, k)
+        for a, b, g in ((aT, bT, gT), (aN, bN, gN), (aL, bL, gL)):
             assert (2 * a, b) in index, (d, i, k, a, b)  # a reduced state of the cycle
             j, S, dj = index[(2 * a, b)]
             assert g == S, (d, i, k, j)                  # with that state's class
@@ -113,7 +113,7 @@ class _Composer:
     def mul(self, d, X, Y, nucomp):
         self.p.stdin.write("%d %d %d %d %d %d %d\n" % ((d,) + X + Y))
         self.p.stdin.flush()
-        okT, aT, bT, gT, okN, aN, bN, gN = map(int, self.p.stdout.readline().split())
+        okT, aT, bT, gT, okN, aN, bN, gN, okL, aL, bL, gL = map(int, self.p.stdout.readline().split())
         ok, out = (okN, (aN, bN, gN)) if nucomp else (okT, (aT, bT, gT))
         assert ok == 1
         return out
@@ -177,3 +177,75 @@ def test_giant_step_search_model_matches_oracle(infra_host, orc, nucomp):
             n += 1
     finally:
         comp.close()
+
+
+def _first_states(d, k):
+    """The first k states (Q_j, P_j, S_j mod 3, delta_j) of the cycle from a_1."""
+    s = math.isqrt(d)
+    rd = math.sqrt(d)
+    P = 2 * ((1 + s) // 2) - 1
+    Q = (d - P * P) // 2
+    S = _c(P)
+    delta = math.log((P + rd) / 2)
+    out = [(Q, P, S % 3, delta)]
+    Qp = 2
+    while len(out) < k:
+        q = (P + s) // Q
+        Pn = q * Q - P
+        Qn = Qp + q * (P - Pn)
+        S += _c(Pn)
+        delta += math.log((Pn + rd) / Q)
+        Qp, P, Q = Q, Pn, Qn
+        out.append((Q, P, S % 3, delta))
+    return out
+
+
+@pytest.mark.parametrize("lo,hi", [(10**6, 10**8), (10**10, 10**11), (10**12, 2 * 10**12),
+                                   (2**44 - 10**10, 2**44)])
+def test_lean_product_lands_on_the_cycle_with_its_class(infra_host, orc, lo, hi):
+    """The search's lean product (fp32 Euclid, c of the second ideal
+    precomputed, residues by float estimates) on random pairs of early cycle
+    states -- equal states (squares) and pairs whose norms share a factor
+    included: a reduced state of the cycle, with that state's class, within
+    log d of the sum of the two distances, and Q_{-1} = (d - P^2)/Q.  Most
+    products equal the textbook composition's term for term (the two can
+    differ by where the reduction stops on an already reduced product)."""
+    rng = np.random.default_rng(lo % 97 + 7)
+    lines, expect = [], []
+    common = 0
+    for d in _pick_d_fast(orc, rng, lo, hi, 8):
+        st = _first_states(d, 1400)  # all inside the first period (_pick_d_fast)
+        index = {(Q, P): (j, S, dl) for j, (Q, P, S, dl) in enumerate(st)}
+        pairs = [tuple(int(x) for x in rng.integers(0, 500, size=2)) for _ in range(150)]
+        pairs += [(5, 5), (40, 40), (0, 0)]
+        for i, k in pairs:
+            (Qi, Pi, Si, di), (Qk, Pk, Sk, dk) = st[i], st[k]
+            common += math.gcd(Qi // 2, Qk // 2) > 1
+            lines.append("%d %d %d %d %d %d %d" % (d, Qi // 2, Pi, Si, Qk // 2, Pk, Sk))
+            expect.append((d, index, di + dk))
+    r = subprocess.run([infra_host], input="\n".join(lines) + "\n", capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    rows = [row for row in r.stdout.split("\n") if row.strip()]
+    assert len(rows) == len(lines)
+    same = 0
+    for line, (d, index, dsum), row in zip(lines, expect, rows):
+        okT, aT, bT, gT, okN, aN, bN, gN, okL, aL, bL, gL = map(int, row.split())
+        assert okT == 1 and okL == 1, line
+        assert (2 * aL, bL) in index, line
+        j, S, dj = index[(2 * aL, bL)]
+        assert gL == S, line
+        assert abs(dj - dsum) <= math.log(d), line
+        same += (aL, bL, gL) == (aT, bT, gT)
+    assert common > 10
+    assert same > 0.9 * len(rows)
+
+
+def _pick_d_fast(orc, rng, lo, hi, k, min_period=1500):
+    """k d in D from [lo, hi) whose period exceeds min_period states."""
+    out = []
+    while len(out) < k:
+        d = int(rng.integers(lo // 8, hi // 8)) * 8 + 5
+        if orc.in_D(d) and orc.walk_mod2(d)[2] > min_period:
+            out.append(d)
+    return out
