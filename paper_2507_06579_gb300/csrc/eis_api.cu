@@ -100,7 +100,7 @@ struct eis_plan {
     // index, the search and the fallback walk
     int bsgs = 0;
     uint32_t bsgs_nbaby = 0, bsgs_chunk = 0, bsgs_rounds = 0;
-    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0;
+    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_grid_index = 0, bsgs_walk_cap = 0;
     float bsgs_tau = 0.0f;
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
@@ -246,13 +246,14 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                         p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_bctr + 2,
                         p->fast);
                     record(p->bev[3 * r + 1], s, capturing);
-                    k_bsgs_index<<<(C + 127) / 128, 128, 0, s>>>(p->d_recs, p->d_bctr + 1, C,
-                                                                  p->d_pool, p->d_steps + 3);
-                    k_bsgs<<<p->bsgs_grid_b, 128, 0, s>>>(
-                        p->d_segs, nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
-                        p->d_flags, p->d_glog, p->d_steps + 1, p->d_status, p->d_fb,
-                        p->d_bctr + 4, C, p->bsgs_tau, c->giant_compose, kBsgsMaxCycles,
-                        p->bsgs_walk_cap, p->fast);
+                    k_bsgs_index<<<p->bsgs_grid_index, 256, 0, s>>>(p->d_segs, nseg, p->d_recs,
+                                                                     p->d_bctr + 1, C, p->d_pool,
+                                                                     p->d_steps + 3);
+                    EIS_CK(launch_k_bsgs(p->bsgs_grid_b, s, p->fast, c->giant_compose, p->d_segs,
+                                         nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
+                                         p->d_flags, p->d_glog, p->d_steps + 1, p->d_status,
+                                         p->d_fb, p->d_bctr + 4, C, p->bsgs_tau, kBsgsMaxCycles,
+                                         p->bsgs_walk_cap));
                     k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_fb, p->d_bctr + 4, p->d_bctr + 5, p->d_flags,
                         p->d_glog, p->d_steps, p->d_status, limit, 0u, nullptr, nullptr, 0u,
@@ -421,6 +422,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
             p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
             p->bsgs_grid_a = (uint32_t)(c->sm_count * c->occ_record);
             p->bsgs_grid_b = (uint32_t)(c->sm_count * c->occ_bsgs);
+            p->bsgs_grid_index = (uint32_t)(c->sm_count * 8);  // 8 warps a block, 8 blocks an SM
             EIS_ALLOC(p->d_pool, (lanes + C) * kBsgsRegionBytes);
             EIS_ALLOC(p->d_recs, C * sizeof(DRecord));
             EIS_ALLOC(p->d_fb, C * 4);
@@ -739,7 +741,9 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
         occ = 1;
     c->occ_record = std::max(1, occ);
     occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bsgs, 128, 0) != cudaSuccess) occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bsgs_kernel(1, EIS_COMPOSE_TEXTBOOK),
+                                                      128, 0) != cudaSuccess)
+        occ = 1;
     c->occ_bsgs = std::max(1, occ);
     cudaGetLastError();
     *out = c;

@@ -60,12 +60,17 @@ struct DEntry {
     uint32_t pad;
 };
 
-// A deferred d handed from the baby walk to the giant-step kernel.
+// A deferred d handed from the baby walk to the giant-step kernel.  The
+// baby walk writes the first four words; the index kernel adds G = a_jl
+// (from entry k-1) and c_G, so that the search reads one record per d.
 struct DRecord {
     uint32_t cand;    // candidate index in the plan layout
-    uint32_t k;       // entries in the table (entry k-1 is G = a_jl)
+    uint32_t k;       // entries in the table (entry k-1 is G); bits 16.. hold G's class
     uint32_t region;  // table region index in the pool
     uint32_t s;       // floor(sqrt d)
+    uint32_t ga;      // G = [ga, (gb + sqrt d)/2]
+    uint32_t gb;
+    int64_t cG;       // (gb^2 - d) / (4 ga)
 };
 
 EIS_HD uint32_t float_bits(float f) {

@@ -39,7 +39,9 @@
 //   l = 2j+1: log eps = 2 S_j + log(P_{j+1});   l = 2j: log eps = 2 S_j.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace eis {
@@ -72,12 +74,42 @@ constexpr uint64_t kFastDLimit = 4390000000000ull;
 constexpr int kErrSteps = 1;  // a baby walk ran past its step limit
 constexpr int kErrGiant = 2;  // a giant-step search failed (table full, no hit)
 
-// floor(sqrt(d)) for d < 2^53: correctly rounded double sqrt, then exact
-// integer fix-ups (at most one step each way).
-__device__ __forceinline__ uint64_t isqrt_u64(uint64_t d) {
-    uint64_t s = (uint64_t)sqrt((double)d);
-    while (s * s > d) --s;
-    while ((s + 1) * (s + 1) <= d) ++s;
+// Exact small integer <-> float by the 2^23 bit pattern (no conversion
+// unit): for 0 <= v < 2^23, the float with bits 0x4B000000 | v is 2^23 + v.
+__host__ __device__ __forceinline__ float u23_to_float(uint32_t v) {
+    uint32_t b = 0x4B000000u | v;
+    float f;
+    memcpy(&f, &b, 4);
+    return f - 8388608.0f;
+}
+
+// floor(sqrt(d)) for d < 2^44 in fp32 and 64-bit integers, without the FP64
+// unit.  float(d) is formed exactly rounded from two 22-bit halves (one
+// rounding, in the FMA); sqrt(float(d)) differs from sqrt(d) by less than
+// sqrt(d) 2^-25 <= 1/8 plus the IEEE square root's rounding (a quarter ulp
+// at most 1/8 here), so its floor is floor(sqrt d) or one off, and one
+// integer correction each way makes it exact.
+__host__ __device__ __forceinline__ uint64_t isqrt44(uint64_t d) {
+    const float hi = u23_to_float((uint32_t)(d >> 22));
+    const float lo = u23_to_float((uint32_t)(d & 0x3FFFFFu));
+#ifdef __CUDA_ARCH__
+    const float fd = __fmaf_rn(hi, 4194304.0f, lo);
+    const float r = __fsqrt_rn(fd);
+    const float fl = __fadd_rd(r, 8388608.0f);  // 2^23 + floor(r), r < 2^22
+#else
+    const float fd = std::fma(hi, 4194304.0f, lo);
+    const float r = std::sqrt(fd);
+    float fl;
+    {
+        const float t = std::floor(r);
+        fl = t + 8388608.0f;  // exact: t < 2^22
+    }
+#endif
+    uint32_t bits;
+    memcpy(&bits, &fl, 4);
+    uint64_t s = bits & 0x7FFFFFu;
+    if (s * s > d) --s;
+    if ((s + 1) * (s + 1) <= d) ++s;
     return s;
 }
 
@@ -136,7 +168,7 @@ __device__ __forceinline__ void walk_park_idle(WalkState &w) {
 // (Q_1 = Q_0 = 2), with *g = log eps_d; otherwise leaves the state at j = 1.
 template <bool kFast>
 __device__ __forceinline__ bool walk_init(uint64_t d, WalkState &w, int &g) {
-    const uint64_t s = isqrt_u64(d);
+    const uint64_t s = isqrt44(d);
     const uint64_t a0 = (1 + s) >> 1;
     const uint64_t P1 = 2 * a0 - 1;
     const uint64_t Q1 = (d - P1 * P1) >> 1;
@@ -230,7 +262,7 @@ __device__ __forceinline__ void lean_park_idle(LeanState &w, float &C) {
 // Returns true when the period is 1, with *g = log eps_d.
 template <bool kFast>
 __device__ __forceinline__ bool lean_init(uint64_t d, LeanState &w, float &C, int &g) {
-    const uint64_t s = isqrt_u64(d);
+    const uint64_t s = isqrt44(d);
     const uint64_t a0 = (1 + s) >> 1;
     const uint64_t P1 = 2 * a0 - 1;
     const uint64_t Q1 = (d - P1 * P1) >> 1;

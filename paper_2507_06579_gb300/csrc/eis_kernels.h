@@ -46,12 +46,16 @@ __global__ void k_walk_record(const Seg *segs, uint32_t nseg, const uint32_t *su
                               unsigned long long *steps_acc, int *status, uint32_t step_limit,
                               uint32_t nbaby, float tau, DRecord *recs, uint32_t *nrec,
                               uint32_t rec_cap, unsigned char *pool, uint32_t *pool_next, int fast);
-__global__ void k_bsgs_index(const DRecord *recs, const uint32_t *nrec, uint32_t rec_cap,
-                             unsigned char *pool, unsigned long long *handed);
-__global__ void k_bsgs(const Seg *segs, uint32_t nseg, const DRecord *recs, const uint32_t *nrec,
-                       uint32_t rec_cap, uint32_t *next_ptr, const unsigned char *pool,
-                       uint32_t *flags, uint8_t *glog, unsigned long long *acc, int *status,
-                       uint32_t *fb_list, uint32_t *fb_count, uint32_t fb_cap, float tau,
-                       int compose, uint32_t max_cycles, uint32_t walk_cap, int fast);
+__global__ void k_bsgs_index(const Seg *segs, uint32_t nseg, DRecord *recs, const uint32_t *nrec,
+                             uint32_t rec_cap, unsigned char *pool, unsigned long long *handed);
+// The lane search kernel for (fast quotient, composition), and its launch
+// (128 threads a block).
+const void *k_bsgs_kernel(int fast, int compose);
+cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose, const Seg *segs,
+                          uint32_t nseg, const DRecord *recs, const uint32_t *nrec, uint32_t rec_cap,
+                          uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
+                          uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
+                          uint32_t *fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
+                          uint32_t walk_cap);
 
 }  // namespace eis

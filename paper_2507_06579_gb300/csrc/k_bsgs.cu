@@ -191,13 +191,9 @@ __device__ __forceinline__ void walk_record_body(
                 if (jl >= (uint32_t)kBsgsMinJl) {
                     const uint32_t slot = atomicAdd(nrec, 1u);
                     if (slot < rec_cap) {
-                        DRecord r;
-                        r.cand = cand;
-                        r.k = k;
-                        r.region = region;
                         // s = floor(sqrt d) from C = 2s (+1), exactly
-                        r.s = (uint32_t)__fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f);
-                        recs[slot] = r;
+                        const uint32_t sv = (uint32_t)__fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f);
+                        *reinterpret_cast<uint4 *>(recs + slot) = make_uint4(cand, k, region, sv);
                         // regions 0 .. grid-1 are the lanes' first ones; the
                         // pool hands out the rest, one per handed-on d
                         region = gridDim.x * blockDim.x + atomicAdd(pool_next, 1u);
@@ -242,33 +238,60 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
                                 pool_next);
 }
 
-// One thread per record: the open-addressing index of its table (the same
-// probing as bsgs_index), built in shared memory and stored after the
-// entries.
-__global__ void __launch_bounds__(128) k_bsgs_index(const DRecord *__restrict__ recs,
+// One warp per record: the open-addressing index of its table (the probing
+// of bsgs_index; concurrent inserts claim empty slots by compare-and-swap
+// on the slot's word in shared memory), stored after the entries; and G =
+// entry k-1 with c_G added to the record.
+__global__ void __launch_bounds__(256) k_bsgs_index(const Seg *__restrict__ segs, uint32_t nseg,
+                                                    DRecord *__restrict__ recs,
                                                     const uint32_t *__restrict__ nrec,
                                                     uint32_t rec_cap, unsigned char *__restrict__ pool,
                                                     unsigned long long *__restrict__ handed) {
-    __shared__ __align__(16) uint8_t sl_all[128 * kBsgsSlots];
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ __align__(16) uint32_t sl_all[8][kBsgsSlots / 4];
     const uint32_t n = min(*nrec, rec_cap);
-    if (r == 0 && handed) atomicAdd(handed, (unsigned long long)n);
-    if (r >= n) return;
-    const DRecord rc = recs[r];
-    unsigned char *base = pool + (size_t)rc.region * kBsgsRegionBytes;
-    const uint4 *e = reinterpret_cast<const uint4 *>(base);
-    uint8_t *sl = sl_all + threadIdx.x * kBsgsSlots;
-    uint32_t *sl32 = reinterpret_cast<uint32_t *>(sl);
-    for (int i = 0; i < kBsgsSlots / 4; ++i) sl32[i] = 0xffffffffu;
-    for (uint32_t i = 0; i < rc.k; ++i) {
-        const uint4 v = e[i];
-        uint32_t p = bsgs_slot(v.x, v.y);
-        while (sl[p] != 0xFF) p = (p + 1) & (kBsgsSlots - 1);
-        sl[p] = (uint8_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && handed) atomicAdd(handed, (unsigned long long)n);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *sl32 = sl_all[wib];
+    for (uint32_t r = blockIdx.x * 8 + wib; r < n; r += gridDim.x * 8) {
+        const uint4 head = *reinterpret_cast<const uint4 *>(recs + r);  // cand, k, region, s
+        const uint32_t k = head.y;
+        unsigned char *base = pool + (size_t)head.z * kBsgsRegionBytes;
+        const uint4 *e = reinterpret_cast<const uint4 *>(base);
+        for (int i = lane; i < kBsgsSlots / 4; i += 32) sl32[i] = 0xffffffffu;
+        __syncwarp();
+        for (uint32_t i = lane; i < k; i += 32) {
+            const uint4 v = e[i];
+            uint32_t p = bsgs_slot(v.x, v.y);
+            for (;;) {
+                const uint32_t w = p >> 2, sh = 8 * (p & 3);
+                const uint32_t cur = sl32[w];
+                if (((cur >> sh) & 0xFFu) != 0xFFu) {
+                    p = (p + 1) & (kBsgsSlots - 1);  // taken: next slot
+                    continue;
+                }
+                const uint32_t nw = (cur & ~(0xFFu << sh)) | (i << sh);
+                if (atomicCAS(&sl32[w], cur, nw) == cur) break;  // else the word changed: retry
+            }
+        }
+        __syncwarp();
+        uint2 *dst = reinterpret_cast<uint2 *>(base + kBsgsKmax * kBsgsEntryBytes);
+        dst[lane] = make_uint2(sl32[2 * lane], sl32[2 * lane + 1]);
+        if (lane == 0) {
+            const uint4 ge = e[k - 1];
+            const int64_t s = (int64_t)head.w;
+            Ideal G;
+            G.a = (int64_t)__uint_as_float(ge.x) / 2;
+            G.b = (int64_t)__uint_as_float(ge.y) - s;  // floor(P + s (+ 1/2)) - s = P
+            G.g = (int)(ge.z % 3u);
+            const int64_t d = (int64_t)cand_to_d(segs, nseg, head.x);
+            DRecord &rc = recs[r];
+            rc.k = k | ((uint32_t)G.g << 16);
+            rc.ga = (uint32_t)G.a;
+            rc.gb = (uint32_t)G.b;
+            rc.cG = lean_cG(G, d);
+        }
+        __syncwarp();
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(base + kBsgsKmax * kBsgsEntryBytes);
-    const uint4 *src = reinterpret_cast<const uint4 *>(sl);
-    for (int i = 0; i < kBsgsSlots / 16; ++i) dst[i] = src[i];
 }
 
 namespace {
@@ -315,20 +338,20 @@ __device__ __forceinline__ void bsgs_body(
             if (!active) {
                 const uint32_t idx = base + __popc(need & lt);
                 if (idx < n) {
-                    const DRecord rc = recs[idx];
-                    cand = rc.cand;
+                    const uint4 r0 = *reinterpret_cast<const uint4 *>(recs + idx);
+                    const uint4 r1 = *(reinterpret_cast<const uint4 *>(recs + idx) + 1);
+                    cand = r0.x;
                     d = (int64_t)cand_to_d(segs, nseg, cand);
-                    s = (int64_t)rc.s;
-                    if (kCompose == 1) L = (int64_t)isqrt_u64((uint64_t)s);
+                    s = (int64_t)r0.w;
+                    if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
                     C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
                     T = __fmul_rn(tau, __uint2float_rn((uint32_t)s));
-                    tab = reinterpret_cast<const DEntry *>(pool + (size_t)rc.region * kBsgsRegionBytes);
+                    tab = reinterpret_cast<const DEntry *>(pool + (size_t)r0.z * kBsgsRegionBytes);
                     slots = reinterpret_cast<const uint8_t *>(tab + kBsgsKmax);
-                    const uint4 ge = *reinterpret_cast<const uint4 *>(tab + (rc.k - 1));
-                    G.a = (int64_t)__uint_as_float(ge.x) / 2;
-                    G.b = (int64_t)__uint_as_float(ge.y) - s;  // floor(P + s (+ 1/2)) - s = P
-                    G.g = (int)(ge.z % 3u);
-                    if (kCompose == 0) cG = lean_cG(G, d);
+                    G.a = (int64_t)r1.x;
+                    G.b = (int64_t)r1.y;
+                    G.g = (int)(r0.y >> 16);
+                    cG = (int64_t)(((uint64_t)r1.w << 32) | r1.z);
                     mu = G;
                     cycles = 0;
                     active = true;
@@ -418,22 +441,38 @@ __device__ __forceinline__ void bsgs_body(
 
 }  // namespace
 
-__global__ void __launch_bounds__(128) k_bsgs(
+template <bool kFast, int kCompose>
+__global__ void __launch_bounds__(128) k_bsgs_t(
     const Seg *__restrict__ segs, uint32_t nseg, const DRecord *__restrict__ recs,
     const uint32_t *__restrict__ nrec, uint32_t rec_cap, uint32_t *__restrict__ next_ptr,
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
-    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, int compose, uint32_t max_cycles,
-    uint32_t walk_cap, int fast) {
-#define EIS_BSGS_BODY(F, K)                                                                     \
-    bsgs_body<F, K>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc, status, \
-                    fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap)
+    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
+    uint32_t walk_cap) {
+    bsgs_body<kFast, kCompose>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc,
+                               status, fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap);
+}
+
+// One instantiation per (quotient, composition), so that each kernel holds
+// only the code it runs.
+const void *k_bsgs_kernel(int fast, int compose) {
     if (fast) {
-        if (compose == EIS_COMPOSE_NUCOMP) EIS_BSGS_BODY(true, 1); else EIS_BSGS_BODY(true, 0);
-    } else {
-        if (compose == EIS_COMPOSE_NUCOMP) EIS_BSGS_BODY(false, 1); else EIS_BSGS_BODY(false, 0);
+        if (compose == EIS_COMPOSE_NUCOMP) return reinterpret_cast<const void *>(&k_bsgs_t<true, 1>);
+        return reinterpret_cast<const void *>(&k_bsgs_t<true, 0>);
     }
-#undef EIS_BSGS_BODY
+    if (compose == EIS_COMPOSE_NUCOMP) return reinterpret_cast<const void *>(&k_bsgs_t<false, 1>);
+    return reinterpret_cast<const void *>(&k_bsgs_t<false, 0>);
+}
+
+cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose, const Seg *segs,
+                          uint32_t nseg, const DRecord *recs, const uint32_t *nrec, uint32_t rec_cap,
+                          uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
+                          uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
+                          uint32_t *fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
+                          uint32_t walk_cap) {
+    void *args[] = {&segs, &nseg, &recs, &nrec, &rec_cap, &next_ptr, &pool, &flags, &glog,
+                    &acc, &status, &fb_list, &fb_count, &fb_cap, &tau, &max_cycles, &walk_cap};
+    return cudaLaunchKernel(k_bsgs_kernel(fast, compose), dim3(grid), dim3(128), args, 0, st);
 }
 
 }  // namespace eis

@@ -163,9 +163,9 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
     G.a = Ga;
     G.b = Gb;
     G.g = Gg;
-    const int64_t s = (int64_t)isqrt_u64(d);
+    const int64_t s = (int64_t)isqrt44(d);
     const int64_t dd = (int64_t)d;
-    const int64_t L = (int64_t)isqrt_u64((uint64_t)s);  // floor(d^(1/4))
+    const int64_t L = (int64_t)isqrt44((uint64_t)s);  // floor(d^(1/4))
     // ---- lane t: mu = G^(t+1) by a product scan over the lanes (five rounds
     // of shuffles, each a composition on the lanes that receive), the stride
     // G^32 from lane 31, then mu = G^(t+2): six compositions deep.
