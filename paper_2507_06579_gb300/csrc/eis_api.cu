@@ -105,7 +105,7 @@ struct eis_plan {
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
     uint32_t *d_fb = nullptr;
-    uint32_t *d_bctr = nullptr;  // [0] walk head [1] records [2] pool head [3] search head
+    uint32_t *d_bctr = nullptr;  // [0] walk head [1] records [3] search head
                                  // [4] fallbacks [5] fallback walk head
     std::vector<cudaEvent_t> bev;  // per round: start, after the walk, end
     uint64_t bytes = 0;
@@ -243,8 +243,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                     k_walk_record<<<p->bsgs_grid_a, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_surv, p->d_ctr, q_lo, q_hi, p->d_bctr,
                         p->d_flags, p->d_glog, p->d_steps, p->d_status, limit, p->bsgs_nbaby,
-                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_bctr + 2,
-                        p->fast);
+                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->fast);
                     record(p->bev[3 * r + 1], s, capturing);
                     k_bsgs_index<<<p->bsgs_grid_index, 256, 0, s>>>(p->d_segs, nseg, p->d_recs,
                                                                      p->d_bctr + 1, C, p->d_pool,

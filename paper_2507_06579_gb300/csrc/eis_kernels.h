@@ -45,7 +45,7 @@ __global__ void k_walk_record(const Seg *segs, uint32_t nseg, const uint32_t *su
                               uint32_t *next_ptr, uint32_t *flags, uint8_t *glog,
                               unsigned long long *steps_acc, int *status, uint32_t step_limit,
                               uint32_t nbaby, float tau, DRecord *recs, uint32_t *nrec,
-                              uint32_t rec_cap, unsigned char *pool, uint32_t *pool_next, int fast);
+                              uint32_t rec_cap, unsigned char *pool, int fast);
 __global__ void k_bsgs_index(const Seg *segs, uint32_t nseg, DRecord *recs, const uint32_t *nrec,
                              uint32_t rec_cap, unsigned char *pool, unsigned long long *handed);
 // The lane search kernel for (fast quotient, composition), and its launch

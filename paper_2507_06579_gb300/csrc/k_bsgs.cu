@@ -6,7 +6,8 @@
 //                 also records every marked state into the lane's table
 //                 region.  A d whose centre does not come within nbaby steps
 //                 (or whose table fills) is handed on as a DRecord, and the
-//                 lane takes a fresh region from the pool for its next d.
+//                 lane takes the region that belongs to that record's slot
+//                 for its next d.
 //  k_bsgs_index   one thread per handed-on d: the table's hash index, built
 //                 in shared memory and copied next to the entries.
 //  k_bsgs         one d per lane, lanes refilled from the records: each
@@ -56,7 +57,7 @@ __device__ __forceinline__ void walk_record_body(
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
     uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
-    uint32_t rec_cap, unsigned char *__restrict__ pool, uint32_t *__restrict__ pool_next) {
+    uint32_t rec_cap, unsigned char *__restrict__ pool) {
     const uint32_t n_total = *n_surv_ptr;
     const uint32_t q_end = min(n_total, q_hi);
     const int lane = threadIdx.x & 31;
@@ -194,9 +195,10 @@ __device__ __forceinline__ void walk_record_body(
                         // s = floor(sqrt d) from C = 2s (+1), exactly
                         const uint32_t sv = (uint32_t)__fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f);
                         *reinterpret_cast<uint4 *>(recs + slot) = make_uint4(cand, k, region, sv);
-                        // regions 0 .. grid-1 are the lanes' first ones; the
-                        // pool hands out the rest, one per handed-on d
-                        region = gridDim.x * blockDim.x + atomicAdd(pool_next, 1u);
+                        // regions 0 .. lanes-1 are the lanes' first ones;
+                        // region lanes + slot belongs to record slot `slot`,
+                        // whose d has just left its region: the lane takes it
+                        region = gridDim.x * blockDim.x + slot;
                         tab = region_entries(pool, region);
                         handed = true;
                     }
@@ -227,15 +229,14 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
     uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
-    uint32_t rec_cap, unsigned char *__restrict__ pool, uint32_t *__restrict__ pool_next, int fast) {
+    uint32_t rec_cap, unsigned char *__restrict__ pool, int fast) {
     if (fast)
         walk_record_body<true>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
-                               steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool,
-                               pool_next);
+                               steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool);
     else
         walk_record_body<false>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
-                                steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool,
-                                pool_next);
+                                steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap,
+                                pool);
 }
 
 // One warp per record: the open-addressing index of its table (the probing
@@ -257,32 +258,55 @@ __global__ void __launch_bounds__(256) k_bsgs_index(const Seg *__restrict__ segs
         const uint32_t k = head.y;
         unsigned char *base = pool + (size_t)head.z * kBsgsRegionBytes;
         const uint4 *e = reinterpret_cast<const uint4 *>(base);
+        // every entry load of the table in flight at once (k <= 128)
+        uint4 v[kBsgsKmax / 32];
+#pragma unroll
+        for (int t = 0; t < kBsgsKmax / 32; ++t) {
+            const uint32_t i = lane + 32 * t;
+            v[t] = i < k ? e[i] : make_uint4(0u, 0u, 0u, 0u);
+        }
         for (int i = lane; i < kBsgsSlots / 4; i += 32) sl32[i] = 0xffffffffu;
         __syncwarp();
-        for (uint32_t i = lane; i < k; i += 32) {
-            const uint4 v = e[i];
-            uint32_t p = bsgs_slot(v.x, v.y);
-            for (;;) {
-                const uint32_t w = p >> 2, sh = 8 * (p & 3);
-                const uint32_t cur = sl32[w];
-                if (((cur >> sh) & 0xFFu) != 0xFFu) {
-                    p = (p + 1) & (kBsgsSlots - 1);  // taken: next slot
-                    continue;
+#pragma unroll
+        for (int t = 0; t < kBsgsKmax / 32; ++t) {
+            const uint32_t i = lane + 32 * t;
+            if (i < k) {
+                uint32_t p = bsgs_slot(v[t].x, v[t].y);
+                for (;;) {
+                    const uint32_t w = p >> 2, sh = 8 * (p & 3);
+                    const uint32_t cur = sl32[w];
+                    if (((cur >> sh) & 0xFFu) != 0xFFu) {
+                        p = (p + 1) & (kBsgsSlots - 1);  // taken: next slot
+                        continue;
+                    }
+                    const uint32_t nw = (cur & ~(0xFFu << sh)) | (i << sh);
+                    if (atomicCAS(&sl32[w], cur, nw) == cur) break;  // else the word changed: retry
                 }
-                const uint32_t nw = (cur & ~(0xFFu << sh)) | (i << sh);
-                if (atomicCAS(&sl32[w], cur, nw) == cur) break;  // else the word changed: retry
             }
         }
         __syncwarp();
         uint2 *dst = reinterpret_cast<uint2 *>(base + kBsgsKmax * kBsgsEntryBytes);
         dst[lane] = make_uint2(sl32[2 * lane], sl32[2 * lane + 1]);
+        // G = entry k-1, held by lane (k-1) % 32 in v[(k-1) / 32]
+        const uint32_t src = (k - 1) & 31, tg = (k - 1) >> 5;
+        uint32_t gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int t = 0; t < kBsgsKmax / 32; ++t) {
+            if ((uint32_t)t == tg) {
+                gx = v[t].x;
+                gy = v[t].y;
+                gz = v[t].z;
+            }
+        }
+        gx = __shfl_sync(kFull, gx, src);
+        gy = __shfl_sync(kFull, gy, src);
+        gz = __shfl_sync(kFull, gz, src);
         if (lane == 0) {
-            const uint4 ge = e[k - 1];
             const int64_t s = (int64_t)head.w;
             Ideal G;
-            G.a = (int64_t)__uint_as_float(ge.x) / 2;
-            G.b = (int64_t)__uint_as_float(ge.y) - s;  // floor(P + s (+ 1/2)) - s = P
-            G.g = (int)(ge.z % 3u);
+            G.a = (int64_t)__uint_as_float(gx) / 2;
+            G.b = (int64_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
+            G.g = (int)(gz % 3u);
             const int64_t d = (int64_t)cand_to_d(segs, nseg, head.x);
             DRecord &rc = recs[r];
             rc.k = k | ((uint32_t)G.g << 16);
