@@ -100,7 +100,7 @@ struct eis_plan {
     // index, the search and the fallback walk
     int bsgs = 0;
     uint32_t bsgs_nbaby = 0, bsgs_chunk = 0, bsgs_rounds = 0;
-    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_grid_index = 0, bsgs_walk_cap = 0;
+    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0;
     float bsgs_tau = 0.0f;
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
@@ -243,11 +243,9 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                     k_walk_record<<<p->bsgs_grid_a, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_surv, p->d_ctr, q_lo, q_hi, p->d_bctr,
                         p->d_flags, p->d_glog, p->d_steps, p->d_status, limit, p->bsgs_nbaby,
-                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->fast);
+                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_steps + 3,
+                        p->fast);
                     record(p->bev[3 * r + 1], s, capturing);
-                    k_bsgs_index<<<p->bsgs_grid_index, 256, 0, s>>>(p->d_segs, nseg, p->d_recs,
-                                                                     p->d_bctr + 1, C, p->d_pool,
-                                                                     p->d_steps + 3);
                     EIS_CK(launch_k_bsgs(p->bsgs_grid_b, s, p->fast, c->giant_compose, p->d_segs,
                                          nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
                                          p->d_flags, p->d_glog, p->d_steps + 1, p->d_status,
@@ -258,7 +256,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                         p->d_glog, p->d_steps, p->d_status, limit, 0u, nullptr, nullptr, 0u,
                         p->fast);
                     record(p->bev[3 * r + 2], s, capturing);
-                    launches += 4;
+                    launches += 3;
                 }
             } else {
                 k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
@@ -421,7 +419,6 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
             p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
             p->bsgs_grid_a = (uint32_t)(c->sm_count * c->occ_record);
             p->bsgs_grid_b = (uint32_t)(c->sm_count * c->occ_bsgs);
-            p->bsgs_grid_index = (uint32_t)(c->sm_count * 8);  // 8 warps a block, 8 blocks an SM
             EIS_ALLOC(p->d_pool, (lanes + C) * kBsgsRegionBytes);
             EIS_ALLOC(p->d_recs, C * sizeof(DRecord));
             EIS_ALLOC(p->d_fb, C * 4);

@@ -44,11 +44,11 @@
 namespace eis {
 
 constexpr int kBsgsKmax = 128;            // table entries per d, entry 0 included
-constexpr int kBsgsSlots = 256;           // hash slots per d (u8 entry index, 0xFF = empty)
+constexpr int kBsgsSlots = 256;           // hash slots per d
 constexpr int kBsgsMinJl = 256;           // a d is searched only if its last marked state
                                           // is at least this far in (window margin)
 constexpr uint32_t kBsgsEntryBytes = 16;
-constexpr uint32_t kBsgsRegionBytes = kBsgsKmax * kBsgsEntryBytes + kBsgsSlots;  // 2304
+constexpr uint32_t kBsgsRegionBytes = kBsgsKmax * kBsgsEntryBytes;  // 2048: the entries
 
 // One baby-table entry: the fp32 bit patterns of Q_j and of num_j = P_j + s
 // (+ 1/2 on the fast path, as the walk carries it), and S_j (reduced mod 3
@@ -60,17 +60,12 @@ struct DEntry {
     uint32_t pad;
 };
 
-// A deferred d handed from the baby walk to the giant-step kernel.  The
-// baby walk writes the first four words; the index kernel adds G = a_jl
-// (from entry k-1) and c_G, so that the search reads one record per d.
+// A deferred d handed from the baby walk to the giant-step kernel.
 struct DRecord {
     uint32_t cand;    // candidate index in the plan layout
-    uint32_t k;       // entries in the table (entry k-1 is G); bits 16.. hold G's class
+    uint32_t k;       // entries in the table (entry k-1 is G = a_jl)
     uint32_t region;  // table region index in the pool
     uint32_t s;       // floor(sqrt d)
-    uint32_t ga;      // G = [ga, (gb + sqrt d)/2]
-    uint32_t gb;
-    int64_t cG;       // (gb^2 - d) / (4 ga)
 };
 
 EIS_HD uint32_t float_bits(float f) {

@@ -45,9 +45,8 @@ __global__ void k_walk_record(const Seg *segs, uint32_t nseg, const uint32_t *su
                               uint32_t *next_ptr, uint32_t *flags, uint8_t *glog,
                               unsigned long long *steps_acc, int *status, uint32_t step_limit,
                               uint32_t nbaby, float tau, DRecord *recs, uint32_t *nrec,
-                              uint32_t rec_cap, unsigned char *pool, int fast);
-__global__ void k_bsgs_index(const Seg *segs, uint32_t nseg, DRecord *recs, const uint32_t *nrec,
-                             uint32_t rec_cap, unsigned char *pool, unsigned long long *handed);
+                              uint32_t rec_cap, unsigned char *pool,
+                              unsigned long long *handed_acc, int fast);
 // The lane search kernel for (fast quotient, composition), and its launch
 // (128 threads a block).
 const void *k_bsgs_kernel(int fast, int compose);

@@ -8,13 +8,14 @@
 //                 (or whose table fills) is handed on as a DRecord, and the
 //                 lane takes the region that belongs to that record's slot
 //                 for its next d.
-//  k_bsgs_index   one thread per handed-on d: the table's hash index, built
-//                 in shared memory and copied next to the entries.
-//  k_bsgs         one d per lane, lanes refilled from the records: each
-//                 cycle composes mu <- reduce(mu * G), walks baby steps to
-//                 the first marked state x and one step beyond, and looks x
-//                 up under its direct and mirror keys; the next cycle
-//                 composes from state x + 1.  A d the search cannot finish
+//  k_bsgs_t       one d per lane, lanes refilled from the records (the warp
+//                 loads a fresh lane's table coalesced and indexes it as
+//                 fingerprints in that lane's shared memory): each cycle
+//                 composes mu <- reduce(mu * G), walks baby steps to the
+//                 first marked state x and one step beyond, and looks x up
+//                 under its direct and mirror keys (shared-memory probes; a
+//                 fingerprint match is settled by a warp-wide exact scan of
+//                 the entries); the next cycle composes from state x + 1.  A d the search cannot finish
 //                 (reduction or walk past its limits) goes to a fallback
 //                 list that the plain persistent walk finishes.
 #include "eis.h"
@@ -57,7 +58,7 @@ __device__ __forceinline__ void walk_record_body(
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
     uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
-    uint32_t rec_cap, unsigned char *__restrict__ pool) {
+    uint32_t rec_cap, unsigned char *__restrict__ pool, unsigned long long *__restrict__ handed_acc) {
     const uint32_t n_total = *n_surv_ptr;
     const uint32_t q_end = min(n_total, q_hi);
     const int lane = threadIdx.x & 31;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void walk_record_body(
     bool exhausted = q_lo >= q_end;  // warp-uniform
     uint32_t cand = 0;
     uint32_t done = 0;       // steps walked by the current d
-    unsigned long long my_steps = 0;
+    unsigned long long my_steps = 0, my_handed = 0;
     for (;;) {
         for (;;) {
             const unsigned need = __ballot_sync(kFull, !active);
@@ -205,6 +206,7 @@ __device__ __forceinline__ void walk_record_body(
                 }
                 if (handed) {
                     my_steps += done;
+                    ++my_handed;
                     active = false;
                     lean_park_idle(w, C);
                 } else {
@@ -219,6 +221,7 @@ __device__ __forceinline__ void walk_record_body(
         }
     }
     warp_add(steps_acc, my_steps);
+    warp_add(handed_acc, my_handed);
 }
 
 }  // namespace
@@ -229,93 +232,16 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
     uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
-    uint32_t rec_cap, unsigned char *__restrict__ pool, int fast) {
+    uint32_t rec_cap, unsigned char *__restrict__ pool, unsigned long long *__restrict__ handed_acc,
+    int fast) {
     if (fast)
         walk_record_body<true>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
-                               steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool);
+                               steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool,
+                               handed_acc);
     else
         walk_record_body<false>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
                                 steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap,
-                                pool);
-}
-
-// One warp per record: the open-addressing index of its table (the probing
-// of bsgs_index; concurrent inserts claim empty slots by compare-and-swap
-// on the slot's word in shared memory), stored after the entries; and G =
-// entry k-1 with c_G added to the record.
-__global__ void __launch_bounds__(256) k_bsgs_index(const Seg *__restrict__ segs, uint32_t nseg,
-                                                    DRecord *__restrict__ recs,
-                                                    const uint32_t *__restrict__ nrec,
-                                                    uint32_t rec_cap, unsigned char *__restrict__ pool,
-                                                    unsigned long long *__restrict__ handed) {
-    __shared__ __align__(16) uint32_t sl_all[8][kBsgsSlots / 4];
-    const uint32_t n = min(*nrec, rec_cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && handed) atomicAdd(handed, (unsigned long long)n);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *sl32 = sl_all[wib];
-    for (uint32_t r = blockIdx.x * 8 + wib; r < n; r += gridDim.x * 8) {
-        const uint4 head = *reinterpret_cast<const uint4 *>(recs + r);  // cand, k, region, s
-        const uint32_t k = head.y;
-        unsigned char *base = pool + (size_t)head.z * kBsgsRegionBytes;
-        const uint4 *e = reinterpret_cast<const uint4 *>(base);
-        // every entry load of the table in flight at once (k <= 128)
-        uint4 v[kBsgsKmax / 32];
-#pragma unroll
-        for (int t = 0; t < kBsgsKmax / 32; ++t) {
-            const uint32_t i = lane + 32 * t;
-            v[t] = i < k ? e[i] : make_uint4(0u, 0u, 0u, 0u);
-        }
-        for (int i = lane; i < kBsgsSlots / 4; i += 32) sl32[i] = 0xffffffffu;
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < kBsgsKmax / 32; ++t) {
-            const uint32_t i = lane + 32 * t;
-            if (i < k) {
-                uint32_t p = bsgs_slot(v[t].x, v[t].y);
-                for (;;) {
-                    const uint32_t w = p >> 2, sh = 8 * (p & 3);
-                    const uint32_t cur = sl32[w];
-                    if (((cur >> sh) & 0xFFu) != 0xFFu) {
-                        p = (p + 1) & (kBsgsSlots - 1);  // taken: next slot
-                        continue;
-                    }
-                    const uint32_t nw = (cur & ~(0xFFu << sh)) | (i << sh);
-                    if (atomicCAS(&sl32[w], cur, nw) == cur) break;  // else the word changed: retry
-                }
-            }
-        }
-        __syncwarp();
-        uint2 *dst = reinterpret_cast<uint2 *>(base + kBsgsKmax * kBsgsEntryBytes);
-        dst[lane] = make_uint2(sl32[2 * lane], sl32[2 * lane + 1]);
-        // G = entry k-1, held by lane (k-1) % 32 in v[(k-1) / 32]
-        const uint32_t src = (k - 1) & 31, tg = (k - 1) >> 5;
-        uint32_t gx = 0, gy = 0, gz = 0;
-#pragma unroll
-        for (int t = 0; t < kBsgsKmax / 32; ++t) {
-            if ((uint32_t)t == tg) {
-                gx = v[t].x;
-                gy = v[t].y;
-                gz = v[t].z;
-            }
-        }
-        gx = __shfl_sync(kFull, gx, src);
-        gy = __shfl_sync(kFull, gy, src);
-        gz = __shfl_sync(kFull, gz, src);
-        if (lane == 0) {
-            const int64_t s = (int64_t)head.w;
-            Ideal G;
-            G.a = (int64_t)__uint_as_float(gx) / 2;
-            G.b = (int64_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
-            G.g = (int)(gz % 3u);
-            const int64_t d = (int64_t)cand_to_d(segs, nseg, head.x);
-            DRecord &rc = recs[r];
-            rc.k = k | ((uint32_t)G.g << 16);
-            rc.ga = (uint32_t)G.a;
-            rc.gb = (uint32_t)G.b;
-            rc.cG = lean_cG(G, d);
-        }
-        __syncwarp();
-    }
+                                pool, handed_acc);
 }
 
 namespace {
@@ -332,6 +258,47 @@ __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, 
         atomicOr(status, kErrGiant);
 }
 
+// Per-lane fingerprint index of a d's table in shared memory: 256 slots of
+// one byte, 0 = empty, else an 8-bit fingerprint (1..255) of the key stored at
+// the slot its probe sequence reached.  A key whose probe meets no slot with
+// its fingerprint before an empty one is not in the table; a fingerprint
+// match is settled by an exact scan of the entries.
+constexpr int kFpWords = kBsgsSlots / 4;
+
+__device__ __forceinline__ uint32_t fp_of(uint32_t q, uint32_t num) {
+    const uint32_t h = (q * 0x2545F491u) ^ (num * 0x9E3779B9u) ^ (q >> 11);
+    const uint32_t f = (h * 0x85EBCA6Bu) >> 24;
+    return f ? f : 1u;
+}
+
+__device__ __forceinline__ void fp_insert(uint32_t *sl, uint32_t q, uint32_t num) {
+    uint32_t p = bsgs_slot(q, num);
+    const uint32_t f = fp_of(q, num);
+    for (int n = 0; n < kBsgsSlots; ++n) {
+        const uint32_t w = p >> 2, sh = 8 * (p & 3);
+        const uint32_t cur = sl[w];
+        if ((cur >> sh) & 0xFFu) {
+            p = (p + 1) & (kBsgsSlots - 1);  // taken: next slot
+            continue;
+        }
+        if (atomicCAS(&sl[w], cur, cur | (f << sh)) == cur) return;  // else the word changed: retry
+    }
+}
+
+// True when (q, num) may be in the table (a slot on its probe sequence holds
+// its fingerprint), false when it certainly is not.
+__device__ __forceinline__ bool fp_maybe(const uint32_t *sl, uint32_t q, uint32_t num) {
+    uint32_t p = bsgs_slot(q, num);
+    const uint32_t f = fp_of(q, num);
+    for (int n = 0; n < kBsgsSlots; ++n) {
+        const uint32_t b = (sl[p >> 2] >> (8 * (p & 3))) & 0xFFu;
+        if (b == 0) return false;
+        if (b == f) return true;
+        p = (p + 1) & (kBsgsSlots - 1);
+    }
+    return true;
+}
+
 template <bool kFast, int kCompose>
 __device__ __forceinline__ void bsgs_body(
     const Seg *__restrict__ segs, uint32_t nseg, const DRecord *__restrict__ recs,
@@ -339,20 +306,23 @@ __device__ __forceinline__ void bsgs_body(
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
     uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
-    uint32_t walk_cap) {
+    uint32_t walk_cap, uint32_t *__restrict__ fp_all) {
     const uint32_t n = min(*nrec, rec_cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    uint32_t *fp_warp = fp_all + (threadIdx.x & ~31u) * kFpWords;  // lane t's words at t * kFpWords
+    uint32_t *fp_mine = fp_warp + lane * kFpWords;
     bool active = false, exhausted = false;
-    uint32_t cand = 0, cycles = 0;
+    uint32_t cand = 0, cycles = 0, k = 0;
     int64_t d = 0, s = 0, L = 0, cG = 0;
     float T = 0.0f, C = 0.0f;
-    const DEntry *tab = nullptr;
-    const uint8_t *slots = nullptr;
+    const uint4 *tab = nullptr;
     Ideal G{1, 1, 0}, mu{1, 1, 0};
     unsigned long long my_cycles = 0, my_walk = 0;
     for (;;) {
+        // ---- refill idle lanes from the records
         const unsigned need = __ballot_sync(kFull, !active);
+        bool fresh = false;
         if (need && !exhausted) {
             const int leader = __ffs(need) - 1;
             uint32_t base = 0;
@@ -362,25 +332,67 @@ __device__ __forceinline__ void bsgs_body(
             if (!active) {
                 const uint32_t idx = base + __popc(need & lt);
                 if (idx < n) {
-                    const uint4 r0 = *reinterpret_cast<const uint4 *>(recs + idx);
-                    const uint4 r1 = *(reinterpret_cast<const uint4 *>(recs + idx) + 1);
+                    const uint4 r0 = *reinterpret_cast<const uint4 *>(recs + idx);  // cand, k, region, s
                     cand = r0.x;
-                    d = (int64_t)cand_to_d(segs, nseg, cand);
+                    k = r0.y;
+                    tab = reinterpret_cast<const uint4 *>(pool + (size_t)r0.z * kBsgsRegionBytes);
                     s = (int64_t)r0.w;
-                    if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
-                    C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
-                    T = __fmul_rn(tau, __uint2float_rn((uint32_t)s));
-                    tab = reinterpret_cast<const DEntry *>(pool + (size_t)r0.z * kBsgsRegionBytes);
-                    slots = reinterpret_cast<const uint8_t *>(tab + kBsgsKmax);
-                    G.a = (int64_t)r1.x;
-                    G.b = (int64_t)r1.y;
-                    G.g = (int)(r0.y >> 16);
-                    cG = (int64_t)(((uint64_t)r1.w << 32) | r1.z);
-                    mu = G;
-                    cycles = 0;
-                    active = true;
+                    fresh = true;
                 }
             }
+        }
+        // ---- the whole warp indexes each fresh lane's table: entries loaded
+        // coalesced, fingerprints inserted into that lane's slots
+        unsigned pend = __ballot_sync(kFull, fresh);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const uint32_t kk = __shfl_sync(kFull, k, src);
+            const uint4 *e = reinterpret_cast<const uint4 *>(
+                __shfl_sync(kFull, reinterpret_cast<unsigned long long>(tab), src));
+            uint32_t *sl = fp_warp + src * kFpWords;
+            uint4 v[kBsgsKmax / 32];
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t) {
+                const uint32_t i = lane + 32 * t;
+                v[t] = i < kk ? e[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+            sl[lane] = 0u;
+            sl[lane + 32] = 0u;
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t)
+                if (lane + 32 * t < kk) fp_insert(sl, v[t].x, v[t].y);
+            // G = entry kk-1, held by lane (kk-1) % 32 in v[(kk-1) / 32]
+            const uint32_t tg = (kk - 1) >> 5;
+            uint32_t gx = 0, gy = 0, gz = 0;
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t) {
+                if ((uint32_t)t == tg) {
+                    gx = v[t].x;
+                    gy = v[t].y;
+                    gz = v[t].z;
+                }
+            }
+            gx = __shfl_sync(kFull, gx, (kk - 1) & 31);
+            gy = __shfl_sync(kFull, gy, (kk - 1) & 31);
+            gz = __shfl_sync(kFull, gz, (kk - 1) & 31);
+            if (lane == src) {
+                G.a = (int64_t)__uint_as_float(gx) / 2;
+                G.b = (int64_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
+                G.g = (int)(gz % 3u);
+            }
+            __syncwarp();
+        }
+        if (fresh) {
+            d = (int64_t)cand_to_d(segs, nseg, cand);
+            if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
+            if (kCompose == 0) cG = lean_cG(G, d);
+            C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
+            T = __fmul_rn(tau, __uint2float_rn((uint32_t)s));
+            mu = G;
+            cycles = 0;
+            active = true;
         }
         if (!__any_sync(kFull, active)) break;
         // ---- giant step: mu <- reduce(mu * G), with Q_{-1} of the result
@@ -437,18 +449,53 @@ __device__ __forceinline__ void bsgs_body(
             }
         }
         my_walk += walked;
-        if (!active) continue;
-        // ---- look x up: direct key (Q_x, P_x), then mirror key (Q_x, P_{x+1});
+        // ---- look x up: direct key (Q_x, P_x) and mirror key (Q_x, P_{x+1});
         // the lane stands at x + 1, so Q_x = w.Qp and g_x = gc - 1 - x_{x+1}
-        const int gx = gc - 1 - w.x;
+        const uint32_t kq = __float_as_uint(w.Qp), kd = __float_as_uint(numx),
+                       km = __float_as_uint(w.num);
+        const bool maybe = active && (fp_maybe(fp_mine, kq, kd) || fp_maybe(fp_mine, kq, km));
         int g = -1;
-        int e = bsgs_find(tab, slots, __float_as_uint(w.Qp), __float_as_uint(numx));
-        if (e >= 0) {
-            g = (gx - (int)(tab[e].s % 3u) + 3 * 4) % 3;  // x = l + j
-        } else {
-            e = bsgs_find(tab, slots, __float_as_uint(w.Qp), __float_as_uint(w.num));
-            if (e >= 0) g = (gx + (int)(tab[e].s % 3u)) % 3;  // x = l - j
+        // exact scan of the tables of the lanes with a fingerprint match, by
+        // the whole warp
+        unsigned scan = __ballot_sync(kFull, maybe);
+        while (scan) {
+            const int src = __ffs(scan) - 1;
+            scan &= scan - 1;
+            const uint32_t kk = __shfl_sync(kFull, k, src);
+            const uint4 *e = reinterpret_cast<const uint4 *>(
+                __shfl_sync(kFull, reinterpret_cast<unsigned long long>(tab), src));
+            const uint32_t sq = __shfl_sync(kFull, kq, src), sd = __shfl_sync(kFull, kd, src),
+                           sm = __shfl_sync(kFull, km, src);
+            int jd = 0x7fffffff, jm = 0x7fffffff;
+            uint32_t Sd = 0, Sm = 0;
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t) {
+                const uint32_t i = lane + 32 * t;
+                if (i < kk) {
+                    const uint4 v = e[i];
+                    if (v.x == sq && v.y == sd && (int)i < jd) {
+                        jd = (int)i;
+                        Sd = v.z;
+                    }
+                    if (v.x == sq && v.y == sm && (int)i < jm) {
+                        jm = (int)i;
+                        Sm = v.z;
+                    }
+                }
+            }
+            const unsigned hd = __ballot_sync(kFull, jd != 0x7fffffff);
+            const unsigned hm = __ballot_sync(kFull, jm != 0x7fffffff);
+            const uint32_t Sd0 = __shfl_sync(kFull, Sd, hd ? __ffs(hd) - 1 : 0);
+            const uint32_t Sm0 = __shfl_sync(kFull, Sm, hm ? __ffs(hm) - 1 : 0);
+            if (lane == src) {
+                const int gx = gc - 1 - w.x;
+                if (hd)
+                    g = (gx - (int)(Sd0 % 3u) + 3 * 4) % 3;  // x = l + j
+                else if (hm)
+                    g = (gx + (int)(Sm0 % 3u)) % 3;          // x = l - j
+            }
         }
+        if (!active) continue;
         if (g >= 0) {
             record_flag(flags, glog, cand, g);
             my_cycles += cycles;
@@ -473,8 +520,9 @@ __global__ void __launch_bounds__(128) k_bsgs_t(
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
     uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
     uint32_t walk_cap) {
+    __shared__ uint32_t fp_all[128 * kFpWords];  // 32 KB: 256 fingerprint slots per lane
     bsgs_body<kFast, kCompose>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc,
-                               status, fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap);
+                               status, fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap, fp_all);
 }
 
 // One instantiation per (quotient, composition), so that each kernel holds
