@@ -271,10 +271,13 @@ __device__ __forceinline__ uint32_t fp_of(uint32_t q, uint32_t num) {
     return f ? f : 1u;
 }
 
+// Each failed compare-and-swap means another lane's insert landed in that
+// word, so with at most kBsgsKmax entries in kBsgsSlots slots an insert takes
+// fewer than kBsgsSlots + kBsgsKmax iterations; the bound is above that.
 __device__ __forceinline__ void fp_insert(uint32_t *sl, uint32_t q, uint32_t num) {
     uint32_t p = bsgs_slot(q, num);
     const uint32_t f = fp_of(q, num);
-    for (int n = 0; n < kBsgsSlots; ++n) {
+    for (int n = 0; n < 2 * kBsgsSlots; ++n) {
         const uint32_t w = p >> 2, sh = 8 * (p & 3);
         const uint32_t cur = sl[w];
         if ((cur >> sh) & 0xFFu) {
