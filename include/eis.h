@@ -214,6 +214,36 @@ typedef struct {
     int32_t trials;          /* settings timed                                  */
 } eis_tune_result;
 
+/* Per-decade settings of the lane search (EIS_GIANT_LANE): a row covers the
+ * d below its d_hi (rows sorted by d_hi; the last row also covers every larger
+ * d).  nbaby = 0 walks those d to the centre of their period. */
+typedef struct {
+    uint64_t d_hi;
+    int32_t nbaby;       /* baby steps before a d is handed to the search */
+    int32_t mark_every;  /* about 1 state in this many is marked          */
+} eis_tune_row;
+
+#define EIS_TUNE_MAX_ROWS 8
+
+/* Install a table of n <= EIS_TUNE_MAX_ROWS rows (n = 0 removes it).  While a
+ * table is installed, plans take each d's settings from its row instead of
+ * EIS_OPT_GIANT_THRESHOLD / EIS_OPT_MARK_EVERY; the search kernel is the lane
+ * search.  Rows must have increasing d_hi, nbaby >= 0, 2 <= mark_every <= 4096. */
+int eis_set_tune_table(eis_ctx *ctx, const eis_tune_row *rows, size_t n);
+
+/* Copy the installed table into rows (capacity cap); *n_out = its length. */
+int eis_get_tune_table(eis_ctx *ctx, eis_tune_row *rows, size_t cap, size_t *n_out);
+
+/* For every decade [10^k, 10^(k+1)) that meets [d_lo, d_hi): time the walk
+ * alone and the lane search at a grid of (nbaby, mark_every) on the top
+ * 2^21 candidates of the decade inside [d_lo, d_hi), and keep the fastest
+ * (the walk unless a setting is 2% faster; every setting must give the same
+ * count).  The rows found replace those of the installed table for the same
+ * decades (the table keeps at most EIS_TUNE_MAX_ROWS rows, merging equal
+ * neighbours) and are copied to rows_out (capacity cap, *n_out rows). */
+int eis_autotune_decades(eis_ctx *ctx, uint64_t d_lo, uint64_t d_hi, eis_tune_row *rows_out,
+                         size_t cap, size_t *n_out);
+
 /* Time candidate settings (CTAs per SM of the persistent walk, deferral of
  * long walks to the warp-per-d giant-step kernel and its threshold, the
  * giant-step baby count) on the sample [lo, hi) -- a window of the d-range

@@ -105,6 +105,13 @@ def build(force: bool = False) -> str:
     return _build.build(force=force)
 
 
+class TuneRow(ctypes.Structure):
+    _fields_ = [("d_hi", ctypes.c_uint64), ("nbaby", ctypes.c_int32), ("mark_every", ctypes.c_int32)]
+
+
+EIS_TUNE_MAX_ROWS = 8
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("giant_threshold", ctypes.c_int64),
                 ("giant_stride", ctypes.c_int64), ("ms_best", ctypes.c_double),
@@ -150,6 +157,9 @@ SIGNATURES = [
     ("eis_is_eisenstein", _I32, [_VP, _U64, _P(_I32)]),
     ("eis_count_batch", _I32, [_VP, _VP, _VP, _SZ, _VP]),
     ("eis_autotune", _I32, [_VP, _U64, _U64, _P(TuneResult)]),
+    ("eis_set_tune_table", _I32, [_VP, _VP, _SZ]),
+    ("eis_get_tune_table", _I32, [_VP, _VP, _SZ, _P(_SZ)]),
+    ("eis_autotune_decades", _I32, [_VP, _U64, _U64, _VP, _SZ, _P(_SZ)]),
     ("eis_classify_range_noalloc", _I32, [_I32, _U64, _U64, _VP, _VP, _P(_U64), _VP]),
     ("eis_plan_create", _I32, [_VP, _VP, _VP, _SZ, _I32, _P(_VP)]),
     ("eis_plan_create_ex", _I32, [_VP, _VP, _VP, _SZ, _I32, ctypes.c_uint32, _P(_VP)]),
@@ -494,6 +504,31 @@ class Context:
         _check(lib().eis_count_batch(self.handle, lo.ctypes.data, hi.ctypes.data, len(lo),
                                      out.ctypes.data), "eis_count_batch")
         return out[: len(lo)]
+
+    def set_tune_table(self, rows):
+        """Install per-decade lane-search settings: rows of (d_hi, nbaby,
+        mark_every), d_hi increasing (eis_set_tune_table); [] removes them."""
+        arr = (TuneRow * max(len(rows), 1))(*[TuneRow(int(a), int(b), int(c)) for a, b, c in rows])
+        _check(lib().eis_set_tune_table(self.handle, ctypes.addressof(arr), len(rows)),
+               "eis_set_tune_table")
+
+    def tune_table(self):
+        """The installed per-decade settings as (d_hi, nbaby, mark_every) rows."""
+        arr = (TuneRow * EIS_TUNE_MAX_ROWS)()
+        n = ctypes.c_size_t()
+        _check(lib().eis_get_tune_table(self.handle, ctypes.addressof(arr), EIS_TUNE_MAX_ROWS,
+                                        ctypes.byref(n)), "eis_get_tune_table")
+        return [(arr[i].d_hi, arr[i].nbaby, arr[i].mark_every) for i in range(n.value)]
+
+    def autotune_decades(self, lo: int, hi: int):
+        """Time the walk and the lane search per decade of [lo, hi) and keep
+        the fastest settings in the context's table (eis_autotune_decades);
+        returns the rows found, (d_hi, nbaby, mark_every), nbaby = 0 = walk."""
+        arr = (TuneRow * 16)()
+        n = ctypes.c_size_t()
+        _check(lib().eis_autotune_decades(self.handle, int(lo), int(hi), ctypes.addressof(arr), 16,
+                                          ctypes.byref(n)), "eis_autotune_decades")
+        return [(arr[i].d_hi, arr[i].nbaby, arr[i].mark_every) for i in range(min(n.value, 16))]
 
     def autotune(self, lo: int, hi: int, cache_path: str | None = None) -> dict:
         """Pick the persistent-walk and giant-step settings for the d-range of

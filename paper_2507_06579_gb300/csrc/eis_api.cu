@@ -61,6 +61,7 @@ struct eis_ctx {
     int occ_persistent = 1;
     int occ_record = 1;                     // resident CTAs/SM of k_walk_record
     int occ_bsgs = 1;                       // ... and of k_bsgs
+    std::vector<eis_tune_row> tune;         // per-decade lane-search settings (empty: none)
     eis_stats last{};
 };
 
@@ -99,9 +100,9 @@ struct eis_plan {
     // bsgs_chunk positions; each round runs the recording walk, the table
     // index, the search and the fallback walk
     int bsgs = 0;
-    uint32_t bsgs_nbaby = 0, bsgs_chunk = 0, bsgs_rounds = 0;
+    uint32_t bsgs_chunk = 0, bsgs_rounds = 0;
     uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0;
-    float bsgs_tau = 0.0f;
+    TuneTab tt{};  // the settings each d looks up
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
     uint32_t *d_fb = nullptr;
@@ -242,14 +243,14 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                     EIS_CK(cudaMemsetAsync(p->d_bctr, 0, 8 * sizeof(uint32_t), s));
                     k_walk_record<<<p->bsgs_grid_a, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_surv, p->d_ctr, q_lo, q_hi, p->d_bctr,
-                        p->d_flags, p->d_glog, p->d_steps, p->d_status, limit, p->bsgs_nbaby,
-                        p->bsgs_tau, p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_steps + 3,
+                        p->d_flags, p->d_glog, p->d_steps, p->d_status, limit, p->tt,
+                        p->d_recs, p->d_bctr + 1, C, p->d_pool, p->d_steps + 3,
                         p->fast);
                     record(p->bev[3 * r + 1], s, capturing);
                     EIS_CK(launch_k_bsgs(p->bsgs_grid_b, s, p->fast, c->giant_compose, p->d_segs,
                                          nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
                                          p->d_flags, p->d_glog, p->d_steps + 1, p->d_status,
-                                         p->d_fb, p->d_bctr + 4, C, p->bsgs_tau, kBsgsMaxCycles,
+                                         p->d_fb, p->d_bctr + 4, C, p->tt, kBsgsMaxCycles,
                                          p->bsgs_walk_cap));
                     k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_fb, p->d_bctr + 4, p->d_bctr + 5, p->d_flags,
@@ -396,8 +397,27 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
     EIS_ALLOC(p->d_steps, 4 * sizeof(unsigned long long));
     if (with_log) EIS_ALLOC(p->d_glog, p->total_cand);
     if (flags & EIS_PLAN_CLASSES) EIS_ALLOC(p->d_cls, 3 * nseg * sizeof(unsigned long long) + 8);
-    if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && c->giant_kernel == EIS_GIANT_LANE &&
-        p->total_cand >= kBsgsMinCands) {
+    // the settings each d of the plan takes: the context's tuning table, or
+    // one row of EIS_OPT_GIANT_THRESHOLD / EIS_OPT_MARK_EVERY
+    bool any_search = false;
+    if (!c->tune.empty()) {
+        p->tt.n = (uint32_t)c->tune.size();
+        for (size_t r = 0; r < c->tune.size(); ++r) {
+            p->tt.d_hi[r] = c->tune[r].d_hi;
+            p->tt.nbaby[r] = (uint32_t)c->tune[r].nbaby;
+            p->tt.tau[r] = 1.39f / (float)c->tune[r].mark_every;
+            any_search |= c->tune[r].nbaby > 0;
+        }
+    } else {
+        p->tt.n = 1;
+        p->tt.d_hi[0] = EIS_D_LIMIT;
+        p->tt.nbaby[0] = c->giant_kernel == EIS_GIANT_LANE
+                             ? (uint32_t)std::min<int64_t>(c->giant_threshold, 0xffffffffll)
+                             : 0u;
+        p->tt.tau[0] = 1.39f / (float)c->mark_every;
+        any_search = p->tt.nbaby[0] > 0;
+    }
+    if (mode == EIS_MODE_PERSISTENT && any_search && p->total_cand >= kBsgsMinCands) {
         // lane-per-d search: survivors in rounds of C queue positions; the
         // pool holds one table region per resident lane plus one per d a
         // round can hand on
@@ -412,8 +432,6 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
         C = std::min<uint64_t>(C, fit / 32 * 32);
         if (C >= ((uint64_t)1 << 16) || C >= (p->total_cand + 31) / 32 * 32) {
             p->bsgs = 1;
-            p->bsgs_nbaby = (uint32_t)std::min<int64_t>(c->giant_threshold, 0xffffffffll);
-            p->bsgs_tau = 1.39f / (float)c->mark_every;
             p->bsgs_walk_cap = (uint32_t)c->bsgs_walk_cap;
             p->bsgs_chunk = (uint32_t)C;
             p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
@@ -425,7 +443,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
             EIS_ALLOC(p->d_bctr, 8 * sizeof(uint32_t));
             p->bev.assign(3 * (size_t)p->bsgs_rounds, nullptr);
         }
-    } else if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 &&
+    } else if (mode == EIS_MODE_PERSISTENT && c->giant_threshold > 0 && c->tune.empty() &&
                c->giant_kernel == EIS_GIANT_WARP && p->total_cand > 0) {
         uint64_t dmax = 0;
         for (const Seg &sg : p->segs)
@@ -946,6 +964,124 @@ int eis_plan_destroy(eis_plan *p) {
     cudaSetDevice(p->ctx->device);
     if (p->launched) cudaStreamSynchronize(p->last_stream);
     plan_free(p);
+    return EIS_OK;
+}
+
+static bool tune_rows_valid(const eis_tune_row *rows, size_t n) {
+    if (n > EIS_TUNE_MAX_ROWS) return false;
+    for (size_t r = 0; r < n; ++r) {
+        if (rows[r].nbaby < 0 || rows[r].mark_every < 2 || rows[r].mark_every > 4096) return false;
+        if (r && rows[r].d_hi <= rows[r - 1].d_hi) return false;
+    }
+    return true;
+}
+
+int eis_set_tune_table(eis_ctx *c, const eis_tune_row *rows, size_t n) {
+    if (!c || (n && !rows) || !tune_rows_valid(rows, n)) return EIS_EINVAL;
+    c->tune.assign(rows, rows + n);
+    return EIS_OK;
+}
+
+int eis_get_tune_table(eis_ctx *c, eis_tune_row *rows, size_t cap, size_t *n_out) {
+    if (!c || !n_out || (cap && !rows)) return EIS_EINVAL;
+    *n_out = c->tune.size();
+    for (size_t r = 0; r < c->tune.size() && r < cap; ++r) rows[r] = c->tune[r];
+    return EIS_OK;
+}
+
+// Candidate (nbaby, mark_every) pairs of the decade tuner; {0, 16} is the
+// walk alone.
+static const eis_tune_row kTuneGrid[] = {
+    {0, 0, 16},     {0, 1024, 16}, {0, 2048, 16}, {0, 2048, 32},
+    {0, 3072, 32},  {0, 4096, 32}, {0, 6144, 64}, {0, 8192, 64},
+};
+
+int eis_autotune_decades(eis_ctx *c, uint64_t d_lo, uint64_t d_hi, eis_tune_row *rows_out,
+                         size_t cap, size_t *n_out) {
+    EisNvtxRange range("eis.autotune_decades");
+    if (!c || d_lo >= d_hi || (cap && !rows_out)) return EIS_EINVAL;
+    if (d_hi > EIS_D_LIMIT) return EIS_ERANGE;
+    const std::vector<eis_tune_row> saved = c->tune;
+    const int saved_mode = c->mode;
+    c->mode = EIS_MODE_PERSISTENT;
+    std::vector<eis_tune_row> found;
+    int rc = EIS_OK;
+    uint64_t dec_lo = 1;
+    while (dec_lo * 10 <= d_lo) dec_lo *= 10;
+    for (; dec_lo < d_hi && rc == EIS_OK; dec_lo *= 10) {
+        const uint64_t dec_hi = std::min<uint64_t>(dec_lo * 10, EIS_D_LIMIT);
+        const uint64_t top = std::min(dec_hi, d_hi);
+        const uint64_t bot = std::max(dec_lo, d_lo);
+        if (bot >= top) continue;
+        const uint64_t width = (uint64_t)8 << 21;  // 2^21 candidates
+        const uint64_t slo = top - bot > width ? top - width : bot;
+        uint64_t ref = 0;
+        double best_ms = 1e300, walk_ms = 1e300;
+        eis_tune_row best = kTuneGrid[0];
+        for (const eis_tune_row &cand : kTuneGrid) {
+            eis_tune_row one = cand;
+            one.d_hi = EIS_D_LIMIT;
+            c->tune.assign(1, one);
+            eis_plan *p = nullptr;
+            rc = plan_build(c, &slo, &top, 1, EIS_MODE_PERSISTENT, 0, &p);
+            if (rc != EIS_OK) break;
+            double ms = 1e300;
+            uint64_t count = 0;
+            for (int rep = 0; rep < 2 && rc == EIS_OK; ++rep) {
+                rc = plan_launch(p, c->stream);
+                eis_stats st{};
+                if (rc == EIS_OK) rc = plan_fill_stats(p, &st);
+                if (rc == EIS_OK) {
+                    ms = std::min(ms, st.ms_total);
+                    count = st.in_E;
+                }
+            }
+            plan_free(p);
+            if (rc != EIS_OK) break;
+            if (cand.nbaby == 0) {
+                ref = count;
+                walk_ms = ms;
+            } else if (count != ref) {  // every setting must give the same count
+                rc = EIS_EDEVICE;
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        if (rc != EIS_OK) break;
+        if (best.nbaby && !(best_ms < kTuneMargin * walk_ms)) best = kTuneGrid[0];
+        best.d_hi = dec_hi;
+        found.push_back(best);
+    }
+    c->mode = saved_mode;
+    if (rc != EIS_OK) {
+        c->tune = saved;
+        return rc;
+    }
+    // merge: the rows found replace the saved rows of the same decades
+    std::vector<eis_tune_row> table;
+    const uint64_t lo_cov = found.empty() ? 0 : found.front().d_hi / 10;
+    const uint64_t hi_cov = found.empty() ? 0 : found.back().d_hi;
+    for (const eis_tune_row &r : saved)
+        if (r.d_hi <= lo_cov) table.push_back(r);
+    for (const eis_tune_row &r : found) table.push_back(r);
+    for (const eis_tune_row &r : saved)
+        if (r.d_hi > hi_cov) table.push_back(r);
+    std::vector<eis_tune_row> merged;
+    for (const eis_tune_row &r : table) {
+        if (!merged.empty() && merged.back().nbaby == r.nbaby &&
+            merged.back().mark_every == r.mark_every)
+            merged.back().d_hi = r.d_hi;
+        else
+            merged.push_back(r);
+    }
+    if (merged.size() > EIS_TUNE_MAX_ROWS) merged.resize(EIS_TUNE_MAX_ROWS);
+    if (!merged.empty()) merged.back().d_hi = std::max<uint64_t>(merged.back().d_hi, EIS_D_LIMIT);
+    c->tune = merged;
+    if (n_out) *n_out = found.size();
+    for (size_t r = 0; r < found.size() && r < cap; ++r) rows_out[r] = found[r];
     return EIS_OK;
 }
 

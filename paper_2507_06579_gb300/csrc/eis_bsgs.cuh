@@ -50,6 +50,23 @@ constexpr int kBsgsMinJl = 256;           // a d is searched only if its last ma
 constexpr uint32_t kBsgsEntryBytes = 16;
 constexpr uint32_t kBsgsRegionBytes = kBsgsKmax * kBsgsEntryBytes;  // 2048: the entries
 
+// Per-decade settings of the search, looked up per d: row r covers
+// d < d_hi[r] (the last row every larger d as well).  nbaby = 0 walks the d
+// to its centre without a table.
+constexpr int kTuneRows = 8;
+struct TuneTab {
+    uint64_t d_hi[kTuneRows];
+    uint32_t nbaby[kTuneRows];
+    float tau[kTuneRows];  // marking threshold factor: T = tau * floor(sqrt d)
+    uint32_t n;
+};
+
+EIS_HD int tune_row(const TuneTab &t, uint64_t d) {
+    int r = 0;
+    while (r + 1 < (int)t.n && d >= t.d_hi[r]) ++r;
+    return r;
+}
+
 // One baby-table entry: the fp32 bit patterns of Q_j and of num_j = P_j + s
 // (+ 1/2 on the fast path, as the walk carries it), and S_j (reduced mod 3
 // by the reader).

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "eis_bsgs.cuh"
 #include "eis_common.cuh"
 
 namespace eis {
@@ -39,12 +40,11 @@ __global__ void k_walk_single(uint64_t d, const uint32_t *primes, const uint64_t
                               const uint32_t *sq_flag);
 __global__ void k_sqfree_one(uint64_t d, const uint64_t *sqtab, uint32_t nprimes, uint32_t *flag);
 
-struct DRecord;
 __global__ void k_walk_record(const Seg *segs, uint32_t nseg, const uint32_t *surv,
                               const uint32_t *n_surv_ptr, uint32_t q_lo, uint32_t q_hi,
                               uint32_t *next_ptr, uint32_t *flags, uint8_t *glog,
                               unsigned long long *steps_acc, int *status, uint32_t step_limit,
-                              uint32_t nbaby, float tau, DRecord *recs, uint32_t *nrec,
+                              const __grid_constant__ TuneTab tt, DRecord *recs, uint32_t *nrec,
                               uint32_t rec_cap, unsigned char *pool,
                               unsigned long long *handed_acc, int fast);
 // The lane search kernel for (fast quotient, composition), and its launch
@@ -54,7 +54,7 @@ cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose,
                           uint32_t nseg, const DRecord *recs, const uint32_t *nrec, uint32_t rec_cap,
                           uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
                           uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
-                          uint32_t *fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
-                          uint32_t walk_cap);
+                          uint32_t *fb_count, uint32_t fb_cap, const TuneTab &tt,
+                          uint32_t max_cycles, uint32_t walk_cap);
 
 }  // namespace eis

@@ -57,8 +57,8 @@ __device__ __forceinline__ void walk_record_body(
     const uint32_t *__restrict__ n_surv_ptr, uint32_t q_lo, uint32_t q_hi,
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
-    uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
-    uint32_t rec_cap, unsigned char *__restrict__ pool, unsigned long long *__restrict__ handed_acc) {
+    const TuneTab &tt, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec, uint32_t rec_cap,
+    unsigned char *__restrict__ pool, unsigned long long *__restrict__ handed_acc) {
     const uint32_t n_total = *n_surv_ptr;
     const uint32_t q_end = min(n_total, q_hi);
     const int lane = threadIdx.x & 31;
@@ -69,6 +69,7 @@ __device__ __forceinline__ void walk_record_body(
     float C;
     lean_park_idle(w, C);
     float T = 0.0f;          // marking threshold of the current d
+    uint32_t nbaby = 0;      // baby steps of the current d before it is handed on
     uint32_t k = 0;          // entries recorded
     uint32_t jl = 0;         // position of the last marked state recorded
     bool rec_on = false;     // recording (and handing on) still possible for this d
@@ -99,17 +100,21 @@ __device__ __forceinline__ void walk_record_body(
                     } else {
                         active = true;
                         done = 0;
+                        const int row = tune_row(tt, d);
+                        nbaby = tt.nbaby[row];
                         // s = (C - 1)/2 (fast) or C/2, exactly; T = tau * s as bsgs_threshold
-                        T = __fmul_rn(tau, __fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f));
-                        // entry 0: a_l = O_K again, (2, P_1), class 0
-                        store_entry(tab, 2.0f, w.num, 0u);
+                        T = __fmul_rn(tt.tau[row], __fmul_rn(kFast ? __fsub_rn(C, 1.0f) : C, 0.5f));
                         k = 1;
                         jl = 0;
-                        rec_on = true;
-                        if (w.Q < T) {  // state 1 itself (S_1 = acc)
-                            store_entry(tab + 1, w.Q, w.num, (uint32_t)w.acc);
-                            k = 2;
-                            jl = 1;
+                        rec_on = nbaby > 0;
+                        if (rec_on) {
+                            // entry 0: a_l = O_K again, (2, P_1), class 0
+                            store_entry(tab, 2.0f, w.num, 0u);
+                            if (w.Q < T) {  // state 1 itself (S_1 = acc)
+                                store_entry(tab + 1, w.Q, w.num, (uint32_t)w.acc);
+                                k = 2;
+                                jl = 1;
+                            }
                         }
                     }
                 }
@@ -231,17 +236,17 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
     const uint32_t *__restrict__ n_surv_ptr, uint32_t q_lo, uint32_t q_hi,
     uint32_t *__restrict__ next_ptr, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ steps_acc, int *__restrict__ status, uint32_t step_limit,
-    uint32_t nbaby, float tau, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
+    const __grid_constant__ TuneTab tt, DRecord *__restrict__ recs, uint32_t *__restrict__ nrec,
     uint32_t rec_cap, unsigned char *__restrict__ pool, unsigned long long *__restrict__ handed_acc,
     int fast) {
     if (fast)
         walk_record_body<true>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
-                               steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap, pool,
+                               steps_acc, status, step_limit, tt, recs, nrec, rec_cap, pool,
                                handed_acc);
     else
         walk_record_body<false>(segs, nseg, surv, n_surv_ptr, q_lo, q_hi, next_ptr, flags, glog,
-                                steps_acc, status, step_limit, nbaby, tau, recs, nrec, rec_cap,
-                                pool, handed_acc);
+                                steps_acc, status, step_limit, tt, recs, nrec, rec_cap, pool,
+                                handed_acc);
 }
 
 namespace {
@@ -308,7 +313,7 @@ __device__ __forceinline__ void bsgs_body(
     const uint32_t *__restrict__ nrec, uint32_t rec_cap, uint32_t *__restrict__ next_ptr,
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
-    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
+    uint32_t *__restrict__ fb_count, uint32_t fb_cap, const TuneTab &tt, uint32_t max_cycles,
     uint32_t walk_cap, uint32_t *__restrict__ fp_all) {
     const uint32_t n = min(*nrec, rec_cap);
     const int lane = threadIdx.x & 31;
@@ -392,7 +397,7 @@ __device__ __forceinline__ void bsgs_body(
             if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
             if (kCompose == 0) cG = lean_cG(G, d);
             C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
-            T = __fmul_rn(tau, __uint2float_rn((uint32_t)s));
+            T = __fmul_rn(tt.tau[tune_row(tt, (uint64_t)d)], __uint2float_rn((uint32_t)s));
             mu = G;
             cycles = 0;
             active = true;
@@ -521,11 +526,11 @@ __global__ void __launch_bounds__(128) k_bsgs_t(
     const uint32_t *__restrict__ nrec, uint32_t rec_cap, uint32_t *__restrict__ next_ptr,
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
-    uint32_t *__restrict__ fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
-    uint32_t walk_cap) {
+    uint32_t *__restrict__ fb_count, uint32_t fb_cap, const __grid_constant__ TuneTab tt,
+    uint32_t max_cycles, uint32_t walk_cap) {
     __shared__ uint32_t fp_all[128 * kFpWords];  // 32 KB: 256 fingerprint slots per lane
     bsgs_body<kFast, kCompose>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc,
-                               status, fb_list, fb_count, fb_cap, tau, max_cycles, walk_cap, fp_all);
+                               status, fb_list, fb_count, fb_cap, tt, max_cycles, walk_cap, fp_all);
 }
 
 // One instantiation per (quotient, composition), so that each kernel holds
@@ -543,10 +548,11 @@ cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose,
                           uint32_t nseg, const DRecord *recs, const uint32_t *nrec, uint32_t rec_cap,
                           uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
                           uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
-                          uint32_t *fb_count, uint32_t fb_cap, float tau, uint32_t max_cycles,
-                          uint32_t walk_cap) {
+                          uint32_t *fb_count, uint32_t fb_cap, const TuneTab &tt,
+                          uint32_t max_cycles, uint32_t walk_cap) {
+    TuneTab t = tt;
     void *args[] = {&segs, &nseg, &recs, &nrec, &rec_cap, &next_ptr, &pool, &flags, &glog,
-                    &acc, &status, &fb_list, &fb_count, &fb_cap, &tau, &max_cycles, &walk_cap};
+                    &acc, &status, &fb_list, &fb_count, &fb_cap, &t, &max_cycles, &walk_cap};
     return cudaLaunchKernel(k_bsgs_kernel(fast, compose), dim3(grid), dim3(128), args, 0, st);
 }
 
