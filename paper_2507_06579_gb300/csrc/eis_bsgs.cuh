@@ -47,6 +47,8 @@ constexpr int kBsgsKmax = 128;            // table entries per d, entry 0 includ
 constexpr int kBsgsSlots = 256;           // hash slots per d
 constexpr int kBsgsMinJl = 256;           // a d is searched only if its last marked state
                                           // is at least this far in (window margin)
+constexpr int kBsgsWideGap = 64;          // the wide stride a_jl * a_j' takes the last
+                                          // table state j' <= jl - kBsgsWideGap
 constexpr uint32_t kBsgsEntryBytes = 16;
 constexpr uint32_t kBsgsRegionBytes = kBsgsKmax * kBsgsEntryBytes;  // 2048: the entries
 

@@ -42,8 +42,9 @@ __device__ __forceinline__ DEntry *region_entries(unsigned char *pool, uint32_t 
     return reinterpret_cast<DEntry *>(pool + (size_t)region * kBsgsRegionBytes);
 }
 
-__device__ __forceinline__ void store_entry(DEntry *e, float Q, float num, uint32_t S) {
-    *reinterpret_cast<uint4 *>(e) = make_uint4(__float_as_uint(Q), __float_as_uint(num), S, 0u);
+// An entry: Q, num (fp32 bits), S (class, reduced by the reader), position j.
+__device__ __forceinline__ void store_entry(DEntry *e, float Q, float num, uint32_t S, uint32_t j) {
+    *reinterpret_cast<uint4 *>(e) = make_uint4(__float_as_uint(Q), __float_as_uint(num), S, j);
 }
 
 constexpr int kRecGroup = 10;  // steps per warp vote in the recording walk
@@ -109,9 +110,9 @@ __device__ __forceinline__ void walk_record_body(
                         rec_on = nbaby > 0;
                         if (rec_on) {
                             // entry 0: a_l = O_K again, (2, P_1), class 0
-                            store_entry(tab, 2.0f, w.num, 0u);
+                            store_entry(tab, 2.0f, w.num, 0u, 0u);
                             if (w.Q < T) {  // state 1 itself (S_1 = acc)
-                                store_entry(tab + 1, w.Q, w.num, (uint32_t)w.acc);
+                                store_entry(tab + 1, w.Q, w.num, (uint32_t)w.acc, 1u);
                                 k = 2;
                                 jl = 1;
                             }
@@ -158,9 +159,9 @@ __device__ __forceinline__ void walk_record_body(
                     for (int i = 0; i < kRecGroup; ++i) {
                         a += ws[i].x;
                         if (ws[i].Q < T && k < (uint32_t)kBsgsKmax) {
-                            store_entry(tab + k, ws[i].Q, ws[i].num, (uint32_t)a + st0 + (uint32_t)i);
-                            ++k;
                             jl = st0 + (uint32_t)i + 1;
+                            store_entry(tab + k, ws[i].Q, ws[i].num, (uint32_t)a + st0 + (uint32_t)i, jl);
+                            ++k;
                         }
                     }
                     full = k >= (uint32_t)kBsgsKmax;
@@ -322,10 +323,15 @@ __device__ __forceinline__ void bsgs_body(
     uint32_t *fp_mine = fp_warp + lane * kFpWords;
     bool active = false, exhausted = false;
     uint32_t cand = 0, cycles = 0, k = 0;
-    int64_t d = 0, s = 0, L = 0, cG = 0;
+    int64_t d = 0, s = 0, L = 0;
     float T = 0.0f, C = 0.0f;
     const uint4 *tab = nullptr;
-    Ideal G{1, 1, 0}, mu{1, 1, 0};
+    // G = a_jl starts the search; the stride Y is reduce(a_jl * a_j') (taken
+    // by the first cycle from Y = a_j', `first`), or a_jl when no table state
+    // lies kBsgsWideGap steps before jl
+    Ideal G{1, 1, 0}, mu{1, 1, 0}, Y{1, 1, 0};
+    int64_t cY = 0;
+    bool first = false;
     unsigned long long my_cycles = 0, my_walk = 0;
     for (;;) {
         // ---- refill idle lanes from the records
@@ -385,17 +391,49 @@ __device__ __forceinline__ void bsgs_body(
             gx = __shfl_sync(kFull, gx, (kk - 1) & 31);
             gy = __shfl_sync(kFull, gy, (kk - 1) & 31);
             gz = __shfl_sync(kFull, gz, (kk - 1) & 31);
+            const uint32_t jlast = __shfl_sync(kFull, (tg == 0 ? v[0].w : tg == 1 ? v[1].w
+                                                       : tg == 2 ? v[2].w : v[3].w), (kk - 1) & 31);
+            // j' = the last entry (not entry 0, not jl itself) at least
+            // kBsgsWideGap steps before jl
+            uint32_t ej = 0;
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t) {
+                const uint32_t i = lane + 32 * t;
+                if (i >= 1 && i + 1 < kk && v[t].w + kBsgsWideGap <= jlast) ej = max(ej, i);
+            }
+            ej = __reduce_max_sync(kFull, ej);
+            const uint32_t tj = ej >> 5;
+            uint32_t jx = 0, jy = 0, jz = 0;
+#pragma unroll
+            for (int t = 0; t < kBsgsKmax / 32; ++t) {
+                if ((uint32_t)t == tj) {
+                    jx = v[t].x;
+                    jy = v[t].y;
+                    jz = v[t].z;
+                }
+            }
+            jx = __shfl_sync(kFull, jx, ej & 31);
+            jy = __shfl_sync(kFull, jy, ej & 31);
+            jz = __shfl_sync(kFull, jz, ej & 31);
             if (lane == src) {
                 G.a = (int64_t)__uint_as_float(gx) / 2;
                 G.b = (int64_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
                 G.g = (int)(gz % 3u);
+                first = ej > 0;
+                if (first) {
+                    Y.a = (int64_t)__uint_as_float(jx) / 2;
+                    Y.b = (int64_t)__uint_as_float(jy) - s;
+                    Y.g = (int)(jz % 3u);
+                } else {
+                    Y = G;
+                }
             }
             __syncwarp();
         }
         if (fresh) {
             d = (int64_t)cand_to_d(segs, nseg, cand);
             if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
-            if (kCompose == 0) cG = lean_cG(G, d);
+            if (kCompose == 0) cY = lean_cG(Y, d);
             C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
             T = __fmul_rn(tt.tau[tune_row(tt, (uint64_t)d)], __uint2float_rn((uint32_t)s));
             mu = G;
@@ -407,11 +445,15 @@ __device__ __forceinline__ void bsgs_body(
         Ideal nx{1, 1, 0};
         int64_t Qm = 2;
         if (active) {
-            const bool ok = bsgs_giant(kCompose, mu, G, cG, d, s, L, nx, Qm) && ++cycles <= max_cycles;
+            const bool ok = bsgs_giant(kCompose, mu, Y, cY, d, s, L, nx, Qm) && ++cycles <= max_cycles;
             if (!ok) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
                 active = false;
+            } else if (first) {  // the first landing, reduce(a_jl * a_j'), is the stride
+                first = false;
+                Y = nx;
+                if (kCompose == 0) cY = lean_cG(Y, d);
             }
         }
         // ---- walk to the first marked state x and one step beyond; a lane

@@ -3,7 +3,7 @@
 // the continued fraction; the table, its index, the marking threshold, the
 // giant steps (eis_infra.cuh) and the search order are the library's own
 // code.  Reads lines
-//     d N tau compose extra verify
+//     d N tau compose extra verify wide
 // (compose: 0 the lean product, 1 NUCOMP, 2 the general textbook code) and
 // prints one line per d:
 //     status g babysteps cycles walksteps k jl hit
@@ -16,6 +16,8 @@
 // (under both keys) and the next composition starts from state x + 1.  With
 // verify = 1 the whole period is walked first and every hit is checked to
 // lie at position l - j or l + j of the first period (hit = 1 if checked).
+// wide = 1 strides by G' = reduce(a_jl * a_j'), a_j' the last table state at
+// least kBsgsWideGap steps before jl (the kernels' stride), wide = 0 by a_jl.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -53,10 +55,10 @@ static bool step(St &w, int64_t s) {
 }
 
 int main() {
-    long long d_, N, compose, extra, verify;
+    long long d_, N, compose, extra, verify, wide;
     double tau_d;
-    while (std::scanf("%lld %lld %lf %lld %lld %lld", &d_, &N, &tau_d, &compose, &extra, &verify) ==
-           6) {
+    while (std::scanf("%lld %lld %lf %lld %lld %lld %lld", &d_, &N, &tau_d, &compose, &extra,
+                      &verify, &wide) == 7) {
         const int64_t d = d_;
         const int64_t s = isqrt_host(d), L = isqrt_host(s);
         const bool fast = (uint64_t)d < kFastDLimit;
@@ -123,7 +125,20 @@ int main() {
         const DEntry &ge = tab.back();
         const Ideal G{(int64_t)bits_float(ge.q) / 2,
                       (int64_t)bits_float(ge.num) - s, (int)(ge.s % 3)};
-        const int64_t cG = lean_cG(G, d);
+        // the stride Y: a_jl, or reduce(a_jl * a_j') (taken by the first cycle)
+        int ej = -1;
+        if (wide)
+            for (int e = 1; e + 1 < (int)tab.size(); ++e)
+                if ((int64_t)tab[e].pad + kBsgsWideGap <= jl) ej = e;
+        Ideal Y = G;
+        int64_t cY = lean_cG(G, d);
+        Ideal Aj = G;
+        int64_t cAj = cY;
+        if (ej > 0) {
+            Aj = Ideal{(int64_t)bits_float(tab[ej].q) / 2, (int64_t)bits_float(tab[ej].num) - s,
+                       (int)(tab[ej].s % 3)};
+            cAj = lean_cG(Aj, d);
+        }
         Ideal mu = G;
         int64_t cycles = 0, walked = 0;
         int status = -1, hitok = 0;
@@ -134,9 +149,14 @@ int main() {
         for (; cycles < (1 << 20) && status < 0; ++cycles) {
             Ideal nx;
             int64_t Qm = 0;
-            if (!bsgs_giant((int)compose, mu, G, cG, d, s, L, nx, Qm)) {
+            const bool first = cycles == 0 && ej > 0;
+            if (!bsgs_giant((int)compose, mu, first ? Aj : Y, first ? cAj : cY, d, s, L, nx, Qm)) {
                 status = -2;
                 break;
+            }
+            if (first) {  // G' = reduce(a_jl * a_j') is the stride from now on
+                Y = nx;
+                cY = lean_cG(Y, d);
             }
             St v{nx.b, 2 * nx.a, Qm};
             if (verify) {

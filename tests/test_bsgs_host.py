@@ -10,7 +10,8 @@ kernel's order), or walking on for a while (as lanes of a warp that wait
 for each other would).  With
 `verify` the model walks the whole period first and checks that every hit is
 at position l - j (mirror key) or l + j (direct key) of the first period,
-the claim the search's window argument makes."""
+the claim the search's window argument makes (also with the wide stride
+reduce(a_jl a_j'), which nearly fills the window)."""
 import os
 import shutil
 import subprocess
@@ -36,9 +37,10 @@ def bsgs_host(tmp_path_factory):
     return exe
 
 
-def _run(exe, rows):
-    """rows: (d, N, tau, compose, extra, verify) -> list of output tuples."""
-    inp = "".join("%d %d %.9g %d %d %d\n" % r for r in rows)
+def _run(exe, rows, wide=1):
+    """rows: (d, N, tau, compose, extra, verify) -> list of output tuples;
+    wide = 1: the wide stride reduce(a_jl a_j'), 0: a_jl."""
+    inp = "".join("%d %d %.9g %d %d %d %d\n" % (r + (wide,)) for r in rows)
     r = subprocess.run([exe], input=inp, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr
     out = [tuple(int(x) for x in ln.split()) for ln in r.stdout.strip().split("\n")]
@@ -73,9 +75,11 @@ def _check(orc, rows, out, want_verified):
     return searched
 
 
+@pytest.mark.parametrize("wide", [1, 0], ids=["wide_stride", "stride_a_jl"])
 @pytest.mark.parametrize("compose", [0, 1, 2], ids=["lean", "nucomp", "textbook"])
-def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose):
-    """d up to 1e10 (whole periods walkable): every hit at l - j or l + j."""
+def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose, wide):
+    """d up to 1e10 (whole periods walkable): every hit at l - j or l + j,
+    with the stride a_jl and with the wide stride reduce(a_jl a_j')."""
     rng = np.random.default_rng(71 + compose)
     rows = []
     for lo, hi in ((10**8, 10**9), (10**9, 10**10)):
@@ -83,7 +87,7 @@ def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose):
             for N, m in ((300, 8), (640, 16), (1200, 32)):
                 for extra in (-1, 0, 50):
                     rows.append((d, N, 1.39 / m, compose, extra, 1))
-    out = _run(bsgs_host, rows)
+    out = _run(bsgs_host, rows, wide)
     assert _check(orc, rows, out, True) > len(rows) // 2
 
 
