@@ -2,16 +2,21 @@
 """Benchmark: discriminants classified per second near d = 10^11.
 
 One step = one full pass of the hot path (square-free sieve, survivor
-compaction, persistent baby-step walk, per-interval count) over every
+compaction, the recording baby walk and the lane-per-d infrastructure search
+with its fallback walk, round by round, and the per-interval count) over every
 candidate d == 5 (mod 8) of [10^11 - 10^9, 10^11] (1.013e8 square-free
-discriminants), with the plan's inputs resident on the device.  Device time
-comes from CUDA events recorded by the plan on its launch stream; L2 is
-flushed (a 512 MiB write) between steps.
+discriminants), with the plan's inputs resident on the device and the
+search's settings (baby length, marking density) tuned per decade on samples
+outside the window beforehand.  Device time comes from CUDA events recorded
+by the plan on its launch stream; L2 is flushed (a 512 MiB write) between
+steps.
 
 Besides the headline ``value`` (persistent work-stealing form) the JSON line
 carries:
 
 * ``plain``: the one-launch-per-2^24-block kernel on the same window;
+* ``walk_only``: the persistent walk of every d to its centre (no giant
+  steps) on the same window;
 * ``batched``: 4096 seeded intervals in one persistent launch, and the same
   intervals through the plain kernel;
 * ``serving``: p50/p99 latency and throughput of the continuous-batching
@@ -19,7 +24,8 @@ carries:
 * ``membership``: single-query latency through eis_is_eisenstein (giant-step
   kernel with either composition, and the single-lane walk);
 * ``e2e``: the same metric through eis_classify_range with host buffers;
-* ``roofline``: the walk kernel against the derived integer-issue peak;
+* ``roofline``: the dominant kernel (the search, or the walk) against the
+  derived integer-issue peak;
 * ``cpu_baseline``: the CPU oracle timed on a bounded sample;
 * ``clocks``: SM clocks and throttle reasons sampled during the timed steps.
 
@@ -52,6 +58,12 @@ TOP = 10**11
 # two subtractions, the multiply-add of the Q recurrence, two for the Z/3
 # class, two compares for the centre test and two for loop and exit
 OPS_PER_BABY_STEP = 11
+# int32-equivalent operations of one giant step of the lane search (the lean
+# product reduce(mu * G')): an extended Euclid on ~22-bit norms (about 13
+# division steps of quotient, remainder and two cofactor updates, 6 ops
+# each), three residue products (12), the product's assembly (6), the exact
+# division for Q_{-1} (10) and about three reduction steps (11 each)
+OPS_PER_GIANT_STEP = 140
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # offered request rates of the serving leg (req/s) and the cap on requests per rate
 SERVE_RATES = (10.0, 100.0, 1000.0, 3000.0, 10000.0, 30000.0, 100000.0)
@@ -125,13 +137,20 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def walk_source_hash():
-    """SHA-1 (16 hex digits) of the walk kernel's sources with comments and
-    blank lines removed, so that only code changes invalidate a record."""
+KERNEL_SOURCES = {
+    "k_walk_persistent": ("k_walk.cu", "eis_common.cuh"),
+    "k_walk_record": ("k_bsgs.cu", "eis_bsgs.cuh", "eis_common.cuh"),
+    "k_bsgs_t": ("k_bsgs.cu", "eis_bsgs.cuh", "eis_infra.cuh", "eis_common.cuh"),
+}
+
+
+def source_hash(files):
+    """SHA-1 (16 hex digits) of a kernel's sources with comments and blank
+    lines removed, so that only code changes invalidate a record."""
     import hashlib
     import re
     h = hashlib.sha1()
-    for f in ("k_walk.cu", "eis_common.cuh"):
+    for f in files:
         src = open(os.path.join(ROOT, "paper_2507_06579_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -140,14 +159,18 @@ def walk_source_hash():
     return h.hexdigest()[:16]
 
 
-def walk_traffic():
-    """DRAM bytes per launch of the walk kernel from the committed ncu
-    summary, or None when the kernel's code changed since it was taken."""
+def walk_source_hash():
+    return source_hash(KERNEL_SOURCES["k_walk_persistent"])
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes per pass of `kernel` from the committed ncu summary, or
+    None when the kernel's code changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get("k_walk_persistent")
-    if not rec or rec.get("source_sha1_16") != walk_source_hash():
+    rec = json.load(open(path)).get(kernel)
+    if not rec or rec.get("source_sha1_16") != source_hash(KERNEL_SOURCES[kernel]):
         return None
     return rec["bytes_per_launch"]
 
@@ -248,9 +271,18 @@ def main():
     lo, hi = rank_window(rank, int(args.window))
     tuned = None
     if not args.no_autotune:
-        # tune on a 1e8-wide sample just below the window (outside the timed region)
+        # outside the timed region: CTAs per SM of the walk on a 1e8-wide
+        # sample just below the window, then the lane search per decade --
+        # the window's decade on a sample just below the window, and the
+        # decades of the batched intervals (up to 1e12)
         tlo = max(5, lo - 10**8)
         tuned = ctx.autotune(tlo, lo)
+        rows = ctx.autotune_decades(10**6, lo)
+        rows += ctx.autotune_decades(lo + 1, 10**12)
+        tuned["decades"] = [{"d_hi": int(a), "nbaby": int(b), "mark_every": int(m)}
+                            for a, b, m in rows]
+        tuned["table"] = [{"d_hi": int(a), "nbaby": int(b), "mark_every": int(m)}
+                          for a, b, m in ctx.tune_table()]
     plan = ctx.plan_create([lo], [hi], E.EIS_MODE_PERSISTENT)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -282,8 +314,11 @@ def main():
     count = int(plan.counts()[0])
     ms_step = sum(s["ms_total"] for s in sts) / len(sts)
     ms_walk = sum(s["ms_walk"] for s in sts) / len(sts)
+    ms_giant = sum(s["ms_giant"] for s in sts) / len(sts)
     nD = sts[0]["in_D"]
     steps_per_launch = sts[0]["baby_steps"]
+    search_steps = sts[0]["search_steps"]
+    giant_per_launch = sts[0]["giant_steps"]
     launches = sts[0]["launches"] * args.steps
 
     # max over ranks of the per-step time, sum of the work
@@ -310,6 +345,24 @@ def main():
         plain = {"value": nD * world / (pms / 1e3), "ms_per_step": pms,
                  "launches_per_step": psts[0]["launches"], "steps": args.plain_steps}
         pplan.destroy()
+
+    # the persistent walk alone (every d walked to its centre) on the same window
+    walk_only = None
+    if args.plain_steps > 0:
+        saved = ctx.tune_table()
+        ctx.set_tune_table([])
+        thr = ctx.get_option(E.EIS_OPT_GIANT_THRESHOLD)
+        ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, 0)
+        wplan = ctx.plan_create([lo], [hi], E.EIS_MODE_PERSISTENT)
+        one(wplan)
+        wsts = [one(wplan) for _ in range(args.plain_steps)]
+        assert int(wplan.counts()[0]) == count
+        wms = sum(s["ms_total"] for s in wsts) / len(wsts)
+        walk_only = {"value": nD * world / (wms / 1e3), "ms_per_step": wms,
+                     "baby_steps_per_step": wsts[0]["baby_steps"], "steps": args.plain_steps}
+        wplan.destroy()
+        ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, thr)
+        ctx.set_tune_table(saved)
 
     # batched uneven ranges: 4096 seeded intervals in one persistent launch,
     # against the same intervals through the plain kernel
@@ -444,16 +497,28 @@ def main():
            "api": "eis_classify_range (host output buffers; plan build, graph capture, "
                   "copies and sync inside the timed call)"}
 
-    ops = OPS_PER_BABY_STEP * steps_per_launch
-    achieved = ops / (ms_walk / 1e3) / 1e9
     peak = SMS * LANES * SM_MAX_MHZ * 1e6 / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_walk_persistent",
-            "ops": "%d int32-equivalent ops per rho step x %d rho steps per launch"
-                   % (OPS_PER_BABY_STEP, steps_per_launch),
-            "peak_basis": "152 SMs x 128 lanes x 2070 MHz (of derived peak)"}
-    roof["traffic"] = walk_traffic()
+    if giant_per_launch and ms_giant >= ms_walk:
+        # the lane search dominates: its baby steps and giant steps
+        ops = OPS_PER_BABY_STEP * search_steps + OPS_PER_GIANT_STEP * giant_per_launch
+        achieved = ops / (ms_giant / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak, "traffic": kernel_traffic("k_bsgs_t"),
+                "kernel": "k_bsgs_t (lane search; fallback walk included)",
+                "ops": "%d ops per baby step x %d steps + %d ops per giant step x %d giant "
+                       "steps per pass" % (OPS_PER_BABY_STEP, search_steps, OPS_PER_GIANT_STEP,
+                                           giant_per_launch),
+                "peak_basis": "152 SMs x 128 lanes x 2070 MHz (of derived peak)"}
+    else:
+        base = steps_per_launch - search_steps
+        ops = OPS_PER_BABY_STEP * base
+        achieved = ops / (ms_walk / 1e3) / 1e9
+        kname = "k_walk_record" if giant_per_launch else "k_walk_persistent"
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak, "traffic": kernel_traffic(kname), "kernel": kname,
+                "ops": "%d int32-equivalent ops per rho step x %d rho steps per pass"
+                       % (OPS_PER_BABY_STEP, base),
+                "peak_basis": "152 SMs x 128 lanes x 2070 MHz (of derived peak)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -470,14 +535,21 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "all square-free d == 5 mod 8 in [1e11-%.0e, 1e11] "
                                        "(per rank: its own window below 1e11)" % args.window,
-                           "mode": "persistent work-stealing walk, CUDA graph",
+                           "mode": "persistent work-stealing recording walk + lane-per-d "
+                                   "infrastructure search per decade (autotuned), CUDA graph",
                            "discriminants_per_step": nD, "candidates_per_step": sts[0]["candidates"],
-                           "baby_steps_per_step": steps_per_launch, "pi_E_window": count,
+                           "baby_steps_per_step": steps_per_launch,
+                           "giant_steps_per_step": giant_per_launch,
+                           "handed_to_search_per_step": sts[0]["deferred"],
+                           "ms_walk_per_step": ms_walk, "ms_search_per_step": ms_giant,
+                           "pi_E_window": count,
                            "l2": "flushed between steps (512 MiB write)",
                            "autotuned": tuned,
                            "parallelism": "dp%d (independent windows)" % world},
                 "plain": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "walk_only": walk_only,
+                "speedup_vs_walk_only": (value / walk_only["value"]) if walk_only else None,
                 "batched": batched,
                 "serving": serving,
                 "membership": membership,

@@ -121,9 +121,12 @@ typedef struct {
     double ms_total;      /* device time of the whole plan (CUDA events) */
     double ms_walk;       /* device time of the walk kernel(s) */
     double ms_sieve;      /* device time of sieve + compaction */
-    double ms_giant;      /* device time of the giant-step kernel */
+    double ms_giant;      /* device time of the giant-step kernel(s) (lane search: */
+                          /* search and fallback walk of every round)           */
     int launches;         /* kernels launched by the plan */
     int sm_count;
+    uint64_t search_steps; /* of baby_steps, those walked by the lane search's   */
+                           /* giant cycles (to their marked states)              */
 } eis_stats;
 
 /* ---------------------------------------------------------------------

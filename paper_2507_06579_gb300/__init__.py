@@ -93,7 +93,8 @@ class Stats(ctypes.Structure):
                 ("giant_steps", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
                 ("ms_total", ctypes.c_double), ("ms_walk", ctypes.c_double),
                 ("ms_sieve", ctypes.c_double), ("ms_giant", ctypes.c_double),
-                ("launches", ctypes.c_int), ("sm_count", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("sm_count", ctypes.c_int),
+                ("search_steps", ctypes.c_uint64)]
 
     def as_dict(self):
         """The fields as a plain dict."""

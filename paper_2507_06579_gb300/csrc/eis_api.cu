@@ -555,6 +555,7 @@ static int plan_fill_stats(eis_plan *p, eis_stats *st) {
         // steps[0]: baby steps of the recording and fallback walks, [1]: steps
         // of the search's walks, [2]: giant cycles, [3]: d handed on
         st->baby_steps = steps[0] + steps[1];
+        st->search_steps = steps[1];
         st->giant_steps = steps[2];
         st->deferred = steps[3];
     }
@@ -619,6 +620,7 @@ static int run_chunks(eis_ctx *c, uint64_t lo, uint64_t hi, int with_log, cudaSt
         acc->in_E += st.in_E;
         acc->baby_steps += st.baby_steps;
         acc->giant_steps += st.giant_steps;
+        acc->search_steps += st.search_steps;
         acc->deferred += st.deferred;
         acc->ms_total += st.ms_total;
         acc->ms_walk += st.ms_walk;

@@ -171,13 +171,31 @@ EIS_HD float fdivmod(float x, float y, float &rem) {
     return q;
 }
 
-// Extended Euclid on 0 <= A, 0 < B < 2^23 in fp32: returns g = gcd(A, B) with
-// xa A + xb B = g.
+// floor(x / y) and the remainder for quotients below 2^22, where the estimate
+// is within one of the quotient: one select-based correction each way.
+EIS_HD float fdivmod1(float x, float y, float &rem) {
+#ifdef __CUDA_ARCH__
+    float q = __fmaf_rd(x, rcp_approx(y), 8388608.0f) - 8388608.0f;
+#else
+    float q = std::floor(x * (1.0f / y));
+#endif
+    float r = x - q * y;
+    const bool lo = r < 0.0f;
+    q = lo ? q - 1.0f : q;
+    r = lo ? r + y : r;
+    const bool hi = r >= y;
+    q = hi ? q + 1.0f : q;
+    rem = hi ? r - y : r;
+    return q;
+}
+
+// Extended Euclid on 0 <= A < 2^22, 0 < B < 2^22 in fp32: returns g = gcd(A, B)
+// with xa A + xb B = g.
 EIS_HD float fegcd(float A, float B, float &xa, float &xb) {
     float r0 = A, r1 = B, a0 = 1.0f, a1 = 0.0f, b0 = 0.0f, b1 = 1.0f;
     while (r1 != 0.0f) {
         float rem;
-        const float q = fdivmod(r0, r1, rem);
+        const float q = fdivmod1(r0, r1, rem);
         r0 = r1;
         r1 = rem;
         const float ta = a0 - q * a1, tb = b0 - q * b1;  // |cofactors| <= B, A: exact
