@@ -278,7 +278,7 @@ def main():
         tlo = max(5, lo - 10**8)
         tuned = ctx.autotune(tlo, lo)
         rows = ctx.autotune_decades(10**6, lo)
-        rows += ctx.autotune_decades(lo + 1, 10**12)
+        rows += ctx.autotune_decades(max(lo + 1, 10**11), 10**12)
         tuned["decades"] = [{"d_hi": int(a), "nbaby": int(b), "mark_every": int(m)}
                             for a, b, m in rows]
         tuned["table"] = [{"d_hi": int(a), "nbaby": int(b), "mark_every": int(m)}

@@ -209,12 +209,16 @@ int eis_count_batch(eis_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t
 
 typedef struct {
     int32_t ctas_per_sm;     /* persistent walk CTAs per SM chosen */
-    int64_t giant_threshold; /* baby steps before a walk goes to the giant-step */
-                             /* kernel (0: never), i.e. 1 or 32 threads per d   */
-    int64_t giant_stride;    /* giant-step baby count N (0: automatic)         */
+    int64_t giant_threshold; /* baby steps before a walk goes to a giant-step  */
+                             /* search (0: never)                               */
+    int64_t giant_stride;    /* warp-per-d search: baby count N (0: automatic)  */
     double ms_best;          /* device time of one pass with the chosen setting */
     double ms_default;       /* ... and with the context's previous setting     */
     int32_t trials;          /* settings timed                                  */
+    int32_t giant_kernel;    /* EIS_GIANT_LANE (1 thread per d) or             */
+                             /* EIS_GIANT_WARP (32 threads per d)               */
+    int32_t mark_every;      /* lane search: marking density (unchanged here)   */
+    int64_t bsgs_chunk;      /* lane search: survivors per round (chunk size)   */
 } eis_tune_result;
 
 /* Per-decade settings of the lane search (EIS_GIANT_LANE): a row covers the
@@ -247,13 +251,15 @@ int eis_get_tune_table(eis_ctx *ctx, eis_tune_row *rows, size_t cap, size_t *n_o
 int eis_autotune_decades(eis_ctx *ctx, uint64_t d_lo, uint64_t d_hi, eis_tune_row *rows_out,
                          size_t cap, size_t *n_out);
 
-/* Time candidate settings (CTAs per SM of the persistent walk, deferral of
- * long walks to the warp-per-d giant-step kernel and its threshold, the
- * giant-step baby count) on the sample [lo, hi) -- a window of the d-range
- * the context will serve -- and keep the fastest in the context, provided it
- * beats the previous setting by more than 2% (else the previous stays).  Every
- * candidate runs a full plan (sieve, walks, count); results are identical
- * for every setting, only time differs.  Takes a few passes of the sample. */
+/* Time candidate settings on the sample [lo, hi) -- a window of the d-range
+ * the context will serve -- with any tuning table set aside: CTAs per SM of
+ * the persistent walk; threads per d (the walk alone, the lane search at one
+ * thread per d, or the warp-per-d kernel at 32 with its threshold); and the
+ * lane search's round size (chunk of survivors).  The fastest stays in the
+ * context, provided it beats the previous setting by more than 2% (else the
+ * previous stays); the table is restored.  Every candidate runs a full plan
+ * (sieve, walks, count); results are identical for every setting, only time
+ * differs.  Takes a few passes of the sample. */
 int eis_autotune(eis_ctx *ctx, uint64_t lo, uint64_t hi, eis_tune_result *out);
 
 /* ---------------------------------------------------------------------

@@ -116,7 +116,9 @@ EIS_TUNE_MAX_ROWS = 8
 class TuneResult(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("giant_threshold", ctypes.c_int64),
                 ("giant_stride", ctypes.c_int64), ("ms_best", ctypes.c_double),
-                ("ms_default", ctypes.c_double), ("trials", ctypes.c_int32)]
+                ("ms_default", ctypes.c_double), ("trials", ctypes.c_int32),
+                ("giant_kernel", ctypes.c_int32), ("mark_every", ctypes.c_int32),
+                ("bsgs_chunk", ctypes.c_int64)]
 
     def as_dict(self):
         """The fields as a plain dict."""
@@ -548,6 +550,9 @@ class Context:
             self.set_option(EIS_OPT_CTAS_PER_SM, r["ctas_per_sm"])
             self.set_option(EIS_OPT_GIANT_THRESHOLD, r["giant_threshold"])
             self.set_option(EIS_OPT_GIANT_STRIDE, r["giant_stride"])
+            if "giant_kernel" in r:
+                self.set_option(EIS_OPT_GIANT_KERNEL, r["giant_kernel"])
+                self.set_option(EIS_OPT_BSGS_CHUNK, r["bsgs_chunk"])
             return dict(r, cached=True)
         res = TuneResult()
         _check(lib().eis_autotune(self.handle, lo, hi, ctypes.byref(res)), "eis_autotune")

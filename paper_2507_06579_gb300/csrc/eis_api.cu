@@ -1079,8 +1079,9 @@ int eis_autotune_decades(eis_ctx *c, uint64_t d_lo, uint64_t d_hi, eis_tune_row 
         else
             merged.push_back(r);
     }
+    // (the last row also covers every larger d; its d_hi stays its decade's
+    // top so that later calls merge by decade)
     if (merged.size() > EIS_TUNE_MAX_ROWS) merged.resize(EIS_TUNE_MAX_ROWS);
-    if (!merged.empty()) merged.back().d_hi = std::max<uint64_t>(merged.back().d_hi, EIS_D_LIMIT);
     c->tune = merged;
     if (n_out) *n_out = found.size();
     for (size_t r = 0; r < found.size() && r < cap; ++r) rows_out[r] = found[r];
@@ -1091,23 +1092,39 @@ int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
     EisNvtxRange range("eis.autotune");
     if (!c || !out || lo >= hi) return EIS_EINVAL;
     if (hi > EIS_D_LIMIT) return EIS_ERANGE;
+    // CTAs per SM of the walk; threads per d (0 = walk only, the lane search
+    // at 1 thread per d, the warp-per-d kernel at 32) with its threshold;
+    // and the round size of the lane search (the chunk of survivors whose
+    // tables one round holds)
     struct Setting {
         int ctas;
-        int64_t thr, stride;
+        int kernel;
+        int64_t thr, chunk;
     };
     const int occ = c->occ_persistent;
     std::vector<Setting> cands;
     for (int ctas : {occ, std::max(1, occ * 3 / 4), std::max(1, occ / 2)})
-        for (int64_t thr : {(int64_t)0, (int64_t)131072, (int64_t)32768})
-            for (int64_t stride : {(int64_t)0, (int64_t)2048})
-                if (thr != 0 || stride == 0) cands.push_back({ctas, thr, stride});
-    const Setting prev{c->ctas_per_sm, c->giant_threshold, c->giant_stride};
+        cands.push_back({ctas, EIS_GIANT_LANE, 0, c->bsgs_chunk});
+    for (int64_t thr : {(int64_t)32768, (int64_t)131072})
+        cands.push_back({occ, EIS_GIANT_WARP, thr, c->bsgs_chunk});
+    const int64_t lane_thr = c->giant_kernel == EIS_GIANT_LANE && c->giant_threshold > 0
+                                 ? c->giant_threshold
+                                 : 2048;
+    for (int64_t chunk : {(int64_t)1 << 20, (int64_t)1 << 21, (int64_t)1 << 22})
+        cands.push_back({occ, EIS_GIANT_LANE, lane_thr, chunk});
+    const Setting prev{c->ctas_per_sm, c->giant_kernel, c->giant_threshold, c->bsgs_chunk};
     const int prev_mode = c->mode;
+    const std::vector<eis_tune_row> saved_table = c->tune;
+    c->tune.clear();  // the trials use the context's global settings
     c->mode = EIS_MODE_PERSISTENT;
-    auto time_one = [&](const Setting &st, double &ms, uint64_t &count) -> int {
+    auto apply = [&](const Setting &st) {
         c->ctas_per_sm = st.ctas;
+        c->giant_kernel = st.kernel;
         c->giant_threshold = st.thr;
-        c->giant_stride = st.stride;
+        c->bsgs_chunk = st.chunk;
+    };
+    auto time_one = [&](const Setting &st, double &ms, uint64_t &count) -> int {
+        apply(st);
         eis_plan *p = nullptr;
         int rc = plan_build(c, &lo, &hi, 1, EIS_MODE_PERSISTENT, 0, &p);
         if (rc != EIS_OK) return rc;
@@ -1150,21 +1167,21 @@ int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
         }
     }
     c->mode = prev_mode;
+    c->tune = saved_table;
     if (rc != EIS_OK) {
-        c->ctas_per_sm = prev.ctas;
-        c->giant_threshold = prev.thr;
-        c->giant_stride = prev.stride;
+        apply(prev);
         return rc;
     }
-    c->ctas_per_sm = best.ctas;
-    c->giant_threshold = best.thr;
-    c->giant_stride = best.stride;
+    apply(best);
     out->ctas_per_sm = best.ctas > 0 ? best.ctas : occ;
     out->giant_threshold = best.thr;
-    out->giant_stride = best.stride;
+    out->giant_stride = c->giant_stride;
     out->ms_best = ms_best;
     out->ms_default = ms_prev;
     out->trials = trials;
+    out->giant_kernel = best.kernel;
+    out->mark_every = c->mark_every;
+    out->bsgs_chunk = best.chunk;
     return EIS_OK;
 }
 
