@@ -78,9 +78,12 @@ def test_single_query_edge_cases(ctx):
 
 @pytest.fixture
 def deferring(ctx):
+    """Plans hand walks past 600 steps to the warp-per-d kernel."""
+    ctx.set_option(E.EIS_OPT_GIANT_KERNEL, E.EIS_GIANT_WARP)
     ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, 600)
     yield ctx
     ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, 0)
+    ctx.set_option(E.EIS_OPT_GIANT_KERNEL, E.EIS_GIANT_LANE)
 
 
 def test_deferral_log_matches_oracle_theta(deferring, orc):
@@ -113,4 +116,5 @@ def test_deferral_table1_and_full_window(deferring):
     assert st["deferred"] > 0
     ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, 0)
     f2, s2, c2 = ctx.classify_range(lo, hi)
+    ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, 600)
     assert c1 == c2 and np.array_equal(f1, f2) and np.array_equal(s1, s2)
