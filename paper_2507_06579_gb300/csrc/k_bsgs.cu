@@ -252,8 +252,10 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
 
 namespace {
 
-// Steps per warp vote while the lanes walk to their marked states.
+// Steps per warp vote while the lanes walk to their marked states, and the
+// steps of one iteration's walk window.
 constexpr int kBsgsGroup = 4;
+constexpr int kBsgsWindow = 32;
 
 __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, uint32_t fb_cap,
                                          uint32_t cand, int *status) {
@@ -332,6 +334,15 @@ __device__ __forceinline__ void bsgs_body(
     Ideal G{1, 1, 0}, mu{1, 1, 0}, Y{1, 1, 0};
     int64_t cY = 0;
     bool first = false;
+    // the lane's walk, carried across iterations: it composes when its last
+    // walk has ended (compose_now), else walks on
+    LeanState w;
+    float Cw = 0.0f;
+    lean_park_idle(w, Cw);
+    int gc = 0;
+    bool at_x = false, compose_now = false;
+    float numx = 0.0f;
+    uint32_t walked = 0;
     unsigned long long my_cycles = 0, my_walk = 0;
     for (;;) {
         // ---- refill idle lanes from the records
@@ -435,75 +446,79 @@ __device__ __forceinline__ void bsgs_body(
             if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
             if (kCompose == 0) cY = lean_cG(Y, d);
             C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
+            Cw = C;
             T = __fmul_rn(tt.tau[tune_row(tt, (uint64_t)d)], __uint2float_rn((uint32_t)s));
             mu = G;
             cycles = 0;
             active = true;
+            compose_now = true;
         }
         if (!__any_sync(kFull, active)) break;
-        // ---- giant step: mu <- reduce(mu * G), with Q_{-1} of the result
-        Ideal nx{1, 1, 0};
-        int64_t Qm = 2;
-        if (active) {
+        // ---- giant step for the lanes whose last walk has ended:
+        // mu <- reduce(mu * Y), with Q_{-1} of the result, and a new walk
+        if (active && compose_now) {
+            Ideal nx{1, 1, 0};
+            int64_t Qm = 2;
             const bool ok = bsgs_giant(kCompose, mu, Y, cY, d, s, L, nx, Qm) && ++cycles <= max_cycles;
             if (!ok) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
                 active = false;
-            } else if (first) {  // the first landing, reduce(a_jl * a_j'), is the stride
-                first = false;
-                Y = nx;
-                if (kCompose == 0) cY = lean_cG(Y, d);
+            } else {
+                if (first) {  // the first landing, reduce(a_jl * a_j'), is the stride
+                    first = false;
+                    Y = nx;
+                    if (kCompose == 0) cY = lean_cG(Y, d);
+                }
+                w.num = bsgs_num(nx.b, s, kFast);
+                w.Q = __uint2float_rn((uint32_t)(2 * nx.a));
+                w.Qp = __uint2float_rn((uint32_t)Qm);
+                w.x = (int)((nx.b >> 1) & 1);
+                w.acc = 0;
+                gc = nx.g;
+                at_x = false;
+                walked = 0;
+                compose_now = false;
             }
         }
-        // ---- walk to the first marked state x and one step beyond; a lane
-        // stops there (at x + 1) while the others finish their walks
-        LeanState w;
-        float Cw = C;
-        int gc = 0;
-        if (active) {
-            w.num = bsgs_num(nx.b, s, kFast);
-            w.Q = __uint2float_rn((uint32_t)(2 * nx.a));
-            w.Qp = __uint2float_rn((uint32_t)Qm);
-            w.x = (int)((nx.b >> 1) & 1);
-            w.acc = 0;
-            gc = nx.g;
-        } else {
-            lean_park_idle(w, Cw);
-        }
-        bool walking = active, at_x = false;
-        float numx = 0.0f;
-        uint32_t walked = 0;
-        while (__any_sync(kFull, walking)) {
+        // ---- walk at most kBsgsWindow steps toward the first marked state x
+        // and one step beyond (a lane stops at x + 1); a walk that needs more
+        // goes on next iteration while the other lanes compose
+        bool walking = active && !compose_now;
+        if (!walking) lean_park_idle(w, Cw);  // idle lanes step NaN states
+        uint32_t stepped = 0;
+        for (int grp = 0; grp < kBsgsWindow / kBsgsGroup && __any_sync(kFull, walking); ++grp) {
 #pragma unroll
             for (int i = 0; i < kBsgsGroup; ++i) {
                 if (walking) {
                     lean_step<kFast>(w, Cw);
                     gc += 1 + w.x;
                     ++walked;
+                    ++stepped;
                     if (at_x) {
                         walking = false;  // at x + 1
+                        compose_now = true;
                     } else if (w.Q < T) {
                         at_x = true;      // at x
                         numx = w.num;
                     }
                 }
             }
-            // a walk that meets no marked state within walk_cap steps gives
-            // the d up to the fallback walk
-            if (walking && walked >= walk_cap) {
-                fallback(fb_list, fb_count, fb_cap, cand, status);
-                my_cycles += cycles;
-                active = false;
-                walking = false;
-            }
         }
-        my_walk += walked;
-        // ---- look x up: direct key (Q_x, P_x) and mirror key (Q_x, P_{x+1});
-        // the lane stands at x + 1, so Q_x = w.Qp and g_x = gc - 1 - x_{x+1}
+        my_walk += stepped;
+        if (active && !compose_now && walked >= walk_cap) {
+            // no marked state within walk_cap steps: the fallback walk finishes it
+            fallback(fb_list, fb_count, fb_cap, cand, status);
+            my_cycles += cycles;
+            active = false;
+        }
+        // ---- look x up for the lanes that reached x + 1: direct key
+        // (Q_x, P_x) and mirror key (Q_x, P_{x+1}); the lane stands at x + 1,
+        // so Q_x = w.Qp and g_x = gc - 1 - x_{x+1}
+        const bool at_end = active && compose_now;
         const uint32_t kq = __float_as_uint(w.Qp), kd = __float_as_uint(numx),
                        km = __float_as_uint(w.num);
-        const bool maybe = active && (fp_maybe(fp_mine, kq, kd) || fp_maybe(fp_mine, kq, km));
+        const bool maybe = at_end && (fp_maybe(fp_mine, kq, kd) || fp_maybe(fp_mine, kq, km));
         int g = -1;
         // exact scan of the tables of the lanes with a fingerprint match, by
         // the whole warp
@@ -545,12 +560,12 @@ __device__ __forceinline__ void bsgs_body(
                     g = (gx + (int)(Sm0 % 3u)) % 3;          // x = l - j
             }
         }
-        if (!active) continue;
+        if (!at_end) continue;
         if (g >= 0) {
             record_flag(flags, glog, cand, g);
             my_cycles += cycles;
             active = false;
-        } else {
+        } else {  // the next giant step starts from x + 1
             mu.a = (int64_t)w.Q / 2;
             mu.b = (int64_t)w.num - s;
             mu.g = gc % 3;
