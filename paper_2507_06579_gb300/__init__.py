@@ -69,6 +69,7 @@ EIS_OPT_GIANT_KERNEL = 11
 EIS_OPT_MARK_EVERY = 12
 EIS_OPT_BSGS_CHUNK = 13
 EIS_OPT_BSGS_WALK_CAP = 14
+EIS_OPT_BSGS_WINDOW = 15
 EIS_GIANT_LANE = 0
 EIS_GIANT_WARP = 1
 EIS_COMPOSE_TEXTBOOK = 0

@@ -58,6 +58,7 @@ struct eis_ctx {
     int mark_every = 16;                    // marked states: about 1 in mark_every
     int64_t bsgs_chunk = (int64_t)1 << 21;  // survivors per record/search round
     int64_t bsgs_walk_cap = 1 << 14;        // steps a giant cycle's walk may take
+    int64_t bsgs_window = 0;                // steps a lane walks per search iteration (0: no limit)
     int occ_persistent = 1;
     int occ_record = 1;                     // resident CTAs/SM of k_walk_record
     int occ_bsgs = 1;                       // ... and of k_bsgs
@@ -101,7 +102,7 @@ struct eis_plan {
     // index, the search and the fallback walk
     int bsgs = 0;
     uint32_t bsgs_chunk = 0, bsgs_rounds = 0;
-    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0;
+    uint32_t bsgs_grid_a = 0, bsgs_grid_b = 0, bsgs_walk_cap = 0, bsgs_window = 0;
     TuneTab tt{};  // the settings each d looks up
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
@@ -251,7 +252,7 @@ static int plan_enqueue(eis_plan *p, cudaStream_t s, bool capturing) {
                                          nseg, p->d_recs, p->d_bctr + 1, C, p->d_bctr + 3, p->d_pool,
                                          p->d_flags, p->d_glog, p->d_steps + 1, p->d_status,
                                          p->d_fb, p->d_bctr + 4, C, p->tt, kBsgsMaxCycles,
-                                         p->bsgs_walk_cap));
+                                         p->bsgs_walk_cap, p->bsgs_window));
                     k_walk_persistent<<<p->walk_grid, 256, 0, s>>>(
                         p->d_segs, nseg, p->d_fb, p->d_bctr + 4, p->d_bctr + 5, p->d_flags,
                         p->d_glog, p->d_steps, p->d_status, limit, 0u, nullptr, nullptr, 0u,
@@ -433,6 +434,7 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
         if (C >= ((uint64_t)1 << 16) || C >= (p->total_cand + 31) / 32 * 32) {
             p->bsgs = 1;
             p->bsgs_walk_cap = (uint32_t)c->bsgs_walk_cap;
+            p->bsgs_window = (uint32_t)(c->bsgs_window > 0 ? c->bsgs_window : c->bsgs_walk_cap);
             p->bsgs_chunk = (uint32_t)C;
             p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
             p->bsgs_grid_a = (uint32_t)(c->sm_count * c->occ_record);
@@ -829,6 +831,10 @@ int eis_set_option(eis_ctx *c, int key, int64_t v) {
             if (v < 1 || v > ((int64_t)1 << 24)) return EIS_EINVAL;
             c->bsgs_walk_cap = v;
             return EIS_OK;
+        case EIS_OPT_BSGS_WINDOW:
+            if (v < 0 || v > ((int64_t)1 << 24)) return EIS_EINVAL;
+            c->bsgs_window = v;
+            return EIS_OK;
         default:
             return EIS_EINVAL;
     }
@@ -849,6 +855,7 @@ int eis_get_option(eis_ctx *c, int key, int64_t *v) {
         case EIS_OPT_MARK_EVERY: *v = c->mark_every; return EIS_OK;
         case EIS_OPT_BSGS_CHUNK: *v = c->bsgs_chunk; return EIS_OK;
         case EIS_OPT_BSGS_WALK_CAP: *v = c->bsgs_walk_cap; return EIS_OK;
+        case EIS_OPT_BSGS_WINDOW: *v = c->bsgs_window; return EIS_OK;
         case EIS_OPT_MEM_BUDGET: *v = (int64_t)c->budget; return EIS_OK;
         case EIS_OPT_MEM_IN_USE: *v = (int64_t)c->in_use.load(); return EIS_OK;
         default: return EIS_EINVAL;

@@ -55,6 +55,6 @@ cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose,
                           uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
                           uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
                           uint32_t *fb_count, uint32_t fb_cap, const TuneTab &tt,
-                          uint32_t max_cycles, uint32_t walk_cap);
+                          uint32_t max_cycles, uint32_t walk_cap, uint32_t walk_window);
 
 }  // namespace eis

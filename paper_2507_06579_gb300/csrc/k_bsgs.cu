@@ -252,10 +252,11 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
 
 namespace {
 
-// Steps per warp vote while the lanes walk to their marked states, and the
-// steps of one iteration's walk window.
+// Steps per warp vote while the lanes walk to their marked states.
 constexpr int kBsgsGroup = 4;
-constexpr int kBsgsWindow = 32;
+// A refill also brings into L2 the table of the record this many positions
+// further on, which some lane will take shortly.
+constexpr uint32_t kPrefetchAhead = 8192;
 
 __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, uint32_t fb_cap,
                                          uint32_t cand, int *status) {
@@ -317,14 +318,15 @@ __device__ __forceinline__ void bsgs_body(
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
     uint32_t *__restrict__ fb_count, uint32_t fb_cap, const TuneTab &tt, uint32_t max_cycles,
-    uint32_t walk_cap, uint32_t *__restrict__ fp_all) {
+    uint32_t walk_cap, uint32_t walk_window, uint32_t *__restrict__ fp_all) {
     const uint32_t n = min(*nrec, rec_cap);
+    const uint32_t groups = (walk_window + kBsgsGroup - 1) / kBsgsGroup;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     uint32_t *fp_warp = fp_all + (threadIdx.x & ~31u) * kFpWords;  // lane t's words at t * kFpWords
     uint32_t *fp_mine = fp_warp + lane * kFpWords;
     bool active = false, exhausted = false;
-    uint32_t cand = 0, cycles = 0, k = 0;
+    uint32_t cand = 0, cycles = 0, k = 0, region_ahead = 0xffffffffu;
     int64_t d = 0, s = 0, L = 0;
     float T = 0.0f, C = 0.0f;
     const uint4 *tab = nullptr;
@@ -357,6 +359,8 @@ __device__ __forceinline__ void bsgs_body(
             if (!active) {
                 const uint32_t idx = base + __popc(need & lt);
                 if (idx < n) {
+                    region_ahead = idx + kPrefetchAhead < n ? recs[idx + kPrefetchAhead].region
+                                                            : 0xffffffffu;
                     const uint4 r0 = *reinterpret_cast<const uint4 *>(recs + idx);  // cand, k, region, s
                     cand = r0.x;
                     k = r0.y;
@@ -384,6 +388,12 @@ __device__ __forceinline__ void bsgs_body(
             }
             sl[lane] = 0u;
             sl[lane + 32] = 0u;
+            // 16 lanes bring the table kPrefetchAhead records on into L2
+            const uint32_t ra = __shfl_sync(kFull, region_ahead, src);
+            if (ra != 0xffffffffu && lane < (int)(kBsgsRegionBytes / 128)) {
+                const unsigned char *pa = pool + (size_t)ra * kBsgsRegionBytes + 128 * lane;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+            }
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < kBsgsKmax / 32; ++t)
@@ -481,13 +491,13 @@ __device__ __forceinline__ void bsgs_body(
                 compose_now = false;
             }
         }
-        // ---- walk at most kBsgsWindow steps toward the first marked state x
+        // ---- walk at most walk_window steps toward the first marked state x
         // and one step beyond (a lane stops at x + 1); a walk that needs more
         // goes on next iteration while the other lanes compose
         bool walking = active && !compose_now;
         if (!walking) lean_park_idle(w, Cw);  // idle lanes step NaN states
         uint32_t stepped = 0;
-        for (int grp = 0; grp < kBsgsWindow / kBsgsGroup && __any_sync(kFull, walking); ++grp) {
+        for (uint32_t grp = 0; grp < groups && __any_sync(kFull, walking); ++grp) {
 #pragma unroll
             for (int i = 0; i < kBsgsGroup; ++i) {
                 if (walking) {
@@ -584,10 +594,11 @@ __global__ void __launch_bounds__(128) k_bsgs_t(
     const unsigned char *__restrict__ pool, uint32_t *__restrict__ flags, uint8_t *__restrict__ glog,
     unsigned long long *__restrict__ acc, int *__restrict__ status, uint32_t *__restrict__ fb_list,
     uint32_t *__restrict__ fb_count, uint32_t fb_cap, const __grid_constant__ TuneTab tt,
-    uint32_t max_cycles, uint32_t walk_cap) {
+    uint32_t max_cycles, uint32_t walk_cap, uint32_t walk_window) {
     __shared__ uint32_t fp_all[128 * kFpWords];  // 32 KB: 256 fingerprint slots per lane
     bsgs_body<kFast, kCompose>(segs, nseg, recs, nrec, rec_cap, next_ptr, pool, flags, glog, acc,
-                               status, fb_list, fb_count, fb_cap, tt, max_cycles, walk_cap, fp_all);
+                               status, fb_list, fb_count, fb_cap, tt, max_cycles, walk_cap,
+                               walk_window, fp_all);
 }
 
 // One instantiation per (quotient, composition), so that each kernel holds
@@ -606,10 +617,11 @@ cudaError_t launch_k_bsgs(uint32_t grid, cudaStream_t st, int fast, int compose,
                           uint32_t *next_ptr, const unsigned char *pool, uint32_t *flags,
                           uint8_t *glog, unsigned long long *acc, int *status, uint32_t *fb_list,
                           uint32_t *fb_count, uint32_t fb_cap, const TuneTab &tt,
-                          uint32_t max_cycles, uint32_t walk_cap) {
+                          uint32_t max_cycles, uint32_t walk_cap, uint32_t walk_window) {
     TuneTab t = tt;
     void *args[] = {&segs, &nseg, &recs, &nrec, &rec_cap, &next_ptr, &pool, &flags, &glog,
-                    &acc, &status, &fb_list, &fb_count, &fb_cap, &t, &max_cycles, &walk_cap};
+                    &acc, &status, &fb_list, &fb_count, &fb_cap, &t, &max_cycles, &walk_cap,
+                    &walk_window};
     return cudaLaunchKernel(k_bsgs_kernel(fast, compose), dim3(grid), dim3(128), args, 0, st);
 }
 
