@@ -87,13 +87,13 @@ extern "C" {
 #define EIS_OPT_MARK_EVERY 12    /* lane search: about 1 state in this many is */
                                  /* marked and kept in the baby table (16)     */
 #define EIS_OPT_BSGS_CHUNK 13    /* lane search: survivors per round of record */
-                                 /* walk + search (2^21); sizes the table pool */
+                                 /* walk + search (2^22); sizes the table pool */
 #define EIS_OPT_BSGS_WALK_CAP 14 /* lane search: steps a giant cycle may walk  */
                                  /* without meeting a marked state before its  */
                                  /* d is finished by the plain walk (2^14)     */
 #define EIS_OPT_BSGS_WINDOW 15   /* lane search: steps a lane walks per search */
                                  /* iteration before the warp's composition    */
-                                 /* (0: until every lane's walk has ended)     */
+                                 /* (64; 0: until every lane's walk has ended) */
 
 /* Giant-step searches of plans (EIS_OPT_GIANT_KERNEL).  Both run after
  * EIS_OPT_GIANT_THRESHOLD baby steps without a centre. */
