@@ -30,7 +30,8 @@ carries:
 * ``clocks``: SM clocks and throttle reasons sampled during the timed steps.
 
 Legs can be shortened or skipped (--plain-steps, --batched-steps,
---serve-seconds, --no-e2e, --no-cpu-baseline, --no-autotune, --window).
+--serve-seconds, --no-e2e, --no-cpu-baseline, --no-autotune, --window);
+profiling runs set the search by hand (--nbaby, --mark-every, --bsgs-chunk).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -249,6 +250,12 @@ def main():
                     help="seconds of Poisson arrivals per serving rate (0: skip)")
     ap.add_argument("--window", type=float, default=WINDOW,
                     help="per-rank window width below 1e11 (smaller for profiling runs)")
+    ap.add_argument("--nbaby", type=int, default=0,
+                    help="with --no-autotune: lane search after this many baby steps (0: walk only)")
+    ap.add_argument("--mark-every", type=int, default=32,
+                    help="with --nbaby: about 1 state in this many is marked")
+    ap.add_argument("--bsgs-chunk", type=int, default=0,
+                    help="survivors per round of the lane search (0: the library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3")
@@ -269,6 +276,12 @@ def main():
     E.build()
     ctx = E.Context(local)
     lo, hi = rank_window(rank, int(args.window))
+    if args.nbaby > 0:
+        ctx.set_option(E.EIS_OPT_GIANT_KERNEL, E.EIS_GIANT_LANE)
+        ctx.set_option(E.EIS_OPT_GIANT_THRESHOLD, args.nbaby)
+        ctx.set_option(E.EIS_OPT_MARK_EVERY, args.mark_every)
+    if args.bsgs_chunk > 0:
+        ctx.set_option(E.EIS_OPT_BSGS_CHUNK, args.bsgs_chunk)
     tuned = None
     if not args.no_autotune:
         # outside the timed region: CTAs per SM of the walk on a 1e8-wide
@@ -312,6 +325,15 @@ def main():
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     count = int(plan.counts()[0])
+    if tuned is not None:
+        mode_label = ("persistent work-stealing recording walk + lane-per-d infrastructure "
+                      "search per decade (autotuned), CUDA graph")
+    elif args.nbaby > 0:
+        mode_label = ("persistent work-stealing recording walk + lane-per-d infrastructure "
+                      "search after %d baby steps, 1 state in %d marked (set by hand), CUDA graph"
+                      % (args.nbaby, args.mark_every))
+    else:
+        mode_label = "persistent work-stealing walk of every d to its centre, CUDA graph"
     ms_step = sum(s["ms_total"] for s in sts) / len(sts)
     ms_walk = sum(s["ms_walk"] for s in sts) / len(sts)
     ms_giant = sum(s["ms_giant"] for s in sts) / len(sts)
@@ -535,8 +557,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "all square-free d == 5 mod 8 in [1e11-%.0e, 1e11] "
                                        "(per rank: its own window below 1e11)" % args.window,
-                           "mode": "persistent work-stealing recording walk + lane-per-d "
-                                   "infrastructure search per decade (autotuned), CUDA graph",
+                           "mode": mode_label,
                            "discriminants_per_step": nD, "candidates_per_step": sts[0]["candidates"],
                            "baby_steps_per_step": steps_per_launch,
                            "giant_steps_per_step": giant_per_launch,

@@ -237,10 +237,9 @@ EIS_HD int32_t mulmod22(int32_t a, int32_t b, int32_t m) {
 // Per-d constant of the lean product: c_G = (b_G^2 - d) / (4 a_G).
 EIS_HD int64_t lean_cG(const Ideal &G, int64_t d) { return (G.b * G.b - d) / (4 * G.a); }
 
-// rho steps until reduced, as ideal_reduce, also returning Q_{-1} of the
-// result; class gained, or -1 past max_steps.
-EIS_HD int lean_reduce(int64_t &P, int64_t &Q, int64_t &Qm, int64_t d, int64_t s, int max_steps) {
-    Qm = exact_quot(d, P, Q);
+// rho steps from (P, Q) with Q_{-1} = Qm until reduced, as ideal_reduce;
+// class gained, or -1 past max_steps.
+EIS_HD int lean_rho(int64_t &P, int64_t &Q, int64_t &Qm, int64_t s, int max_steps) {
     int g = 0;
     for (int it = 0; !ideal_is_reduced(P, Q, s); ++it) {
         if (it >= max_steps) return -1;
@@ -253,6 +252,13 @@ EIS_HD int lean_reduce(int64_t &P, int64_t &Q, int64_t &Qm, int64_t d, int64_t s
         Q = Qn;
     }
     return g;
+}
+
+// rho steps until reduced, as ideal_reduce, also returning Q_{-1} of the
+// result; class gained, or -1 past max_steps.
+EIS_HD int lean_reduce(int64_t &P, int64_t &Q, int64_t &Qm, int64_t d, int64_t s, int max_steps) {
+    Qm = exact_quot(d, P, Q);
+    return lean_rho(P, Q, Qm, s, max_steps);
 }
 
 // reduce(mu * G) and Q_{-1} of the result; false if the reduction ran away.
@@ -300,14 +306,188 @@ EIS_HD bool lean_mul(const Ideal &mu, const Ideal &G, int64_t cG, int64_t d, int
     return true;
 }
 
+// ------------------------------------------------------------ lean NUCOMP
+// NUCOMP (Algorithm 2, as ideal_mul_nucomp in eis_infra.cuh) specialised to
+// two reduced ideals of a discriminant d < 2^44.  Every coefficient u, v, w
+// of a reduced form is below sqrt(d) < 2^22 in magnitude (u |w| = (d - P^2)/4
+// with both factors reduced Q's over 2), so both Euclid runs (the gcd of the
+// u's and the partial Euclid that stops below L) work on integers below 2^22
+// in fp32, exactly, with reciprocal quotient estimates and one select-based
+// correction each way.  The closing formulas multiply those small numbers
+// into 64-bit values and divide exactly by a small divisor, each quotient
+// taken from a float estimate rounded to the nearest integer.  The result is
+// near-reduced: about one rho step finishes it, against about six for the
+// textbook product.  The third coefficients are passed in: w = -Q_{-1}/2 of
+// each ideal, which the walk carries.
+
+// float |v| < 2^22 to the nearest int32, and 0 <= v < 2^23 to float, with no
+// conversion instruction
+EIS_HD int32_t fl_to_i(float v) { return (int32_t)(float_bits(v + 12582912.0f) - 0x4B400000u); }
+EIS_HD float i_to_fl(int32_t v) { return u23_to_float((uint32_t)v); }
+
+// n / dv for dv | n, 0 < |dv| < 2^23: the estimate n rcp(dv) has relative
+// error below 2^-22, so while |n / dv| < 2^21 it lies within 1/2 of the
+// quotient and rounds to it; one correction each way guards the bound.
+// Larger quotients take the 64-bit division.
+EIS_HD int64_t exact_div_small(int64_t n, int32_t dv) {
+#ifdef __CUDA_ARCH__
+    const float e = __fmul_rn((float)n, rcp_approx((float)dv));
+#else
+    const float e = (float)n * (1.0f / (float)dv);
+#endif
+    if (!(fabsf(e) < 2097152.0f)) return n / dv;
+    int64_t q = (int64_t)fl_to_i(e);  // nearest integer
+    const int64_t r = n - q * dv;
+    if (r != 0) q += ((r > 0) == (dv > 0)) ? 1 : -1;
+    return q;
+}
+
+// x mod m in [0, m) for |x| < 2^45, 0 < m < 2^22: x = hi 2^23 + lo, and
+// 2^23 mod m = 2 (2^22 mod m) folded once.
+EIS_HD int32_t mod_small(int64_t x, int32_t m) {
+    const int32_t hi = (int32_t)(x >> 23), lo = (int32_t)(x & 0x7FFFFF);
+    int32_t p23 = 2 * fmodp(1 << 22, m);
+    p23 = p23 >= m ? p23 - m : p23;
+    const int32_t r = mulmod22(fmodp(hi, m), p23, m) + fmodp(lo, m);
+    return r >= m ? r - m : r;
+}
+
+// log_omega of gamma mod 2O_K from A, B, C mod 2^32 (gamma_class of
+// eis_infra.cuh in 32-bit words: C = 2 u3 with |u3| < 2^25 has at most 25
+// trailing zeros, so the low 32 bits decide every case alike).
+EIS_HD int gamma_class32(uint32_t A, uint32_t B, uint32_t C, bool &ok) {
+    const uint32_t a = A - B, b = 2u * B;
+#ifdef __CUDA_ARCH__
+    const int ka = a ? __ffs((int)a) - 1 : 32, kb = b ? __ffs((int)b) - 1 : 32;
+    const int kc = C ? __ffs((int)C) - 1 : 32;
+#else
+    const int ka = a ? __builtin_ctz(a) : 32, kb = b ? __builtin_ctz(b) : 32;
+    const int kc = C ? __builtin_ctz(C) : 32;
+#endif
+    const int k = ka < kb ? ka : kb;
+    if (k != kc || k >= 31) {
+        ok = false;
+        return 0;
+    }
+    return f4_log((int)((a >> k) & 1u), (int)((b >> k) & 1u));
+}
+
+// reduce(X * Y) by NUCOMP, with Q_{-1} of the result; wX, wY are the forms'
+// third coefficients (b^2 - d) / (4a) and L = floor(sqrt(floor(sqrt d))).
+// Ideals with a tiny norm, and squares, take the lean textbook product.
+EIS_HD bool lean_nucomp(const Ideal &X, int64_t wX, const Ideal &Y, int64_t wY, int64_t d, int64_t s,
+                        int64_t L, Ideal &out, int64_t &Qm) {
+    int32_t u1 = (int32_t)X.a, v1 = -(int32_t)X.b, w1 = (int32_t)wX;
+    int32_t u2 = (int32_t)Y.a, v2 = -(int32_t)Y.b, w2 = (int32_t)wY;
+    if (u1 <= 50 || u2 <= 50 || (u1 == u2 && v1 == v2)) return lean_mul(X, Y, wY, d, s, out, Qm);
+    if (w1 < w2) {
+        int32_t t = u1; u1 = u2; u2 = t;
+        t = v1; v1 = v2; v2 = t;
+        t = w1; w1 = w2; w2 = t;
+    }
+    const int32_t sp = (v1 + v2) / 2, m = v2 - sp;  // v1 + v2 is even
+    float fb, fc;
+    const int32_t F = fl_to_i(fegcd(i_to_fl(u2), i_to_fl(u1), fb, fc));  // b u2 + c u1 = F
+    const int32_t b = fl_to_i(fb);
+    int32_t G = F, By = u1, Cy = u2, Dy = sp, bx;
+    if (F == 1) {
+        bx = mulmod22(fmodp(m, By), fmodp(b, By), By);  // Bx = m b mod By
+    } else {
+        const int32_t spF = fmodp(sp, F);
+        if (spF != 0) {
+            float xx, yy;
+            G = fl_to_i(fegcd(i_to_fl(F), i_to_fl(spF), xx, yy));  // xx F + yy sp == G (mod F)
+            const int32_t H = F / G, c = fl_to_i(fc);
+            By = u1 / G;
+            Cy = u2 / G;
+            Dy = sp / G;
+            // l = yy (b (w1 mod H) + c (w2 mod H)) mod H; Bx = (b m + l By) / H
+            int32_t t = mulmod22(fmodp(b, H), fmodp(w1, H), H) + mulmod22(fmodp(c, H), fmodp(w2, H), H);
+            t = t >= H ? t - H : t;
+            const int32_t l = mulmod22(fmodp(fl_to_i(yy), H), t, H);
+            const int64_t Bx = exact_div_small((int64_t)b * m + (int64_t)l * By, H);
+            bx = mod_small(Bx, By);
+        } else {
+            By = u1 / F;
+            Cy = u2 / F;
+            Dy = sp / F;
+            bx = mulmod22(fmodp(m, By), fmodp(b, By), By);
+        }
+    }
+    // partial Euclid on (By, bx) down to L, cofactors (x, y), z steps
+    int32_t by, x, y, z = 0;
+    {
+        float fby = i_to_fl(By), fbx = i_to_fl(bx), fx = 1.0f, fy = 0.0f;
+        const float fL = i_to_fl((int32_t)L);
+        while (fby > fL && fbx != 0.0f) {
+            float r;
+            const float q = fdivmod1(fby, fbx, r);
+            fby = fbx;
+            fbx = r;
+            const float t = fy - q * fx;  // |q x| <= By: exact
+            fy = fx;
+            fx = t;
+            ++z;
+        }
+        by = fl_to_i(fby);
+        bx = fl_to_i(fbx);
+        x = fl_to_i(fx);
+        y = fl_to_i(fy);
+    }
+    if (z & 1) {
+        by = -by;
+        y = -y;
+    }
+    int64_t u3, v3, w3;
+    if (z != 0) {
+        const int64_t cx = exact_div_small((int64_t)Cy * bx - (int64_t)m * x, By);
+        const int64_t Q1 = (int64_t)by * cx, Q2 = Q1 + m;
+        const int64_t dx = exact_div_small((int64_t)Dy * bx - (int64_t)w2 * x, By);
+        const int64_t Q3 = (int64_t)y * dx, Q4 = Q3 + Dy;
+        const int64_t dy = exact_div_small(Q4, x);
+        if (bx == 0 && dx == 0) return false;  // (not expected)
+        const int64_t cy = bx != 0 ? exact_div_small(Q2, bx) : (cx * dy - w1) / dx;
+        u3 = (int64_t)by * cy - (int64_t)G * y * dy;
+        w3 = (int64_t)bx * cx - (int64_t)G * x * dx;
+        v3 = (int64_t)G * (Q3 + Q4) - Q1 - Q2;
+    } else {
+        const int64_t Q1 = (int64_t)Cy * bx;
+        const int64_t cx = exact_div_small(Q1 - m, By), dx = exact_div_small((int64_t)bx * Dy - w2, By);
+        u3 = (int64_t)by * Cy;
+        w3 = (int64_t)bx * cx - (int64_t)G * dx;
+        v3 = v2 - 2 * Q1;
+    }
+    // gamma mod 2O_K from A = G (2 u3 x + v3 y), B = G y, C = 2 u3
+    bool ok = true;
+    const uint32_t C2 = 2u * (uint32_t)u3;
+    const int lg = gamma_class32((uint32_t)G * (C2 * (uint32_t)x + (uint32_t)v3 * (uint32_t)y),
+                                 (uint32_t)G * (uint32_t)y, C2, ok);
+    if (!ok || u3 == 0) return false;
+    // the ideal [|u3|, (-v3 + sqrt d)/2]: P0 = -v3 with Q_{-1} = -2 w3 sign(u3),
+    // moved into (s - Q, s] by k Q, which changes Q_{-1} by -k (P0 + P)
+    int64_t Q = 2 * (u3 < 0 ? -u3 : u3);
+    const int64_t P0 = -v3;
+    const int64_t k = floor_div_fast(s - P0, Q);
+    int64_t P = P0 + k * Q;
+    Qm = (u3 > 0 ? -2 * w3 : 2 * w3) - k * (P0 + P);
+    const int gr = lean_rho(P, Q, Qm, s, 256);
+    if (gr < 0) return false;
+    out.a = Q / 2;
+    out.b = P;
+    out.g = (X.g + Y.g + 3 - lg + gr) % 3;
+    return true;
+}
+
 // mu * G reduced, with Q_{-1} = (d - P^2)/Q of the result (the state before
-// it on the cycle): the lean product (compose = 0, the textbook composition
-// of forms), NUCOMP (1), or the general textbook code of eis_infra.cuh (2,
-// the reference the tests compare with).  cG = lean_cG(G, d).
-EIS_HD bool bsgs_giant(int compose, const Ideal &mu, const Ideal &G, int64_t cG, int64_t d,
+// it on the cycle): the lean textbook product (compose = 0), the lean NUCOMP
+// (1), the general textbook code of eis_infra.cuh (2) or its general NUCOMP
+// (3), the last two the references the tests compare with.  wmu and wG are
+// the forms' third coefficients (b^2 - d)/(4a) (lean_cG), L = floor(sqrt s).
+EIS_HD bool bsgs_giant(int compose, const Ideal &mu, int64_t wmu, const Ideal &G, int64_t wG, int64_t d,
                        int64_t s, int64_t L, Ideal &out, int64_t &Qm) {
-    if (compose == 0) return lean_mul(mu, G, cG, d, s, out, Qm);
-    const bool ok = compose == 1 ? ideal_mul_nucomp(mu, G, d, s, L, out) : ideal_mul(mu, G, d, s, out);
+    if (compose == 0) return lean_mul(mu, G, wG, d, s, out, Qm);
+    if (compose == 1) return lean_nucomp(mu, wmu, G, wG, d, s, L, out, Qm);
+    const bool ok = compose == 3 ? ideal_mul_nucomp(mu, G, d, s, L, out) : ideal_mul(mu, G, d, s, out);
     if (!ok) return false;
     Qm = exact_quot(d, out.b, 2 * out.a);
     return true;

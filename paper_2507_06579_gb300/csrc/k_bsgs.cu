@@ -334,7 +334,7 @@ __device__ __forceinline__ void bsgs_body(
     // by the first cycle from Y = a_j', `first`), or a_jl when no table state
     // lies kBsgsWideGap steps before jl
     Ideal G{1, 1, 0}, mu{1, 1, 0}, Y{1, 1, 0};
-    int64_t cY = 0;
+    int64_t wY = 0, wmu = 0;  // third form coefficients (b^2 - d)/(4a) of Y and mu
     bool first = false;
     // the lane's walk, carried across iterations: it composes when its last
     // walk has ended (compose_now), else walks on
@@ -453,8 +453,11 @@ __device__ __forceinline__ void bsgs_body(
         }
         if (fresh) {
             d = (int64_t)cand_to_d(segs, nseg, cand);
-            if (kCompose == 1) L = (int64_t)isqrt44((uint64_t)s);
-            if (kCompose == 0) cY = lean_cG(Y, d);
+            if (kCompose == 1) {
+                L = (int64_t)isqrt44((uint64_t)s);
+                wmu = lean_cG(G, d);
+            }
+            wY = lean_cG(Y, d);
             C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
             Cw = C;
             T = __fmul_rn(tt.tau[tune_row(tt, (uint64_t)d)], __uint2float_rn((uint32_t)s));
@@ -469,7 +472,7 @@ __device__ __forceinline__ void bsgs_body(
         if (active && compose_now) {
             Ideal nx{1, 1, 0};
             int64_t Qm = 2;
-            const bool ok = bsgs_giant(kCompose, mu, Y, cY, d, s, L, nx, Qm) && ++cycles <= max_cycles;
+            const bool ok = bsgs_giant(kCompose, mu, wmu, Y, wY, d, s, L, nx, Qm) && ++cycles <= max_cycles;
             if (!ok) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
@@ -478,7 +481,7 @@ __device__ __forceinline__ void bsgs_body(
                 if (first) {  // the first landing, reduce(a_jl * a_j'), is the stride
                     first = false;
                     Y = nx;
-                    if (kCompose == 0) cY = lean_cG(Y, d);
+                    wY = -Qm / 2;  // (b^2 - d)/(4a) = -Q_{-1}/2
                 }
                 w.num = bsgs_num(nx.b, s, kFast);
                 w.Q = __uint2float_rn((uint32_t)(2 * nx.a));
@@ -579,6 +582,7 @@ __device__ __forceinline__ void bsgs_body(
             mu.a = (int64_t)w.Q / 2;
             mu.b = (int64_t)w.num - s;
             mu.g = gc % 3;
+            wmu = -(int64_t)w.Qp / 2;  // Q_{-1} of x + 1 is Q_x
         }
     }
     warp_add(&acc[0], my_walk);

@@ -4,7 +4,8 @@
 // giant steps (eis_infra.cuh) and the search order are the library's own
 // code.  Reads lines
 //     d N tau compose extra verify wide
-// (compose: 0 the lean product, 1 NUCOMP, 2 the general textbook code) and
+// (compose: 0 the lean textbook product, 1 the lean NUCOMP, 2 the general
+// textbook code, 3 the general NUCOMP) and
 // prints one line per d:
 //     status g babysteps cycles walksteps k jl hit
 // status 0 = centre reached in the baby walk (g = log eps_d), 1 = found by
@@ -140,6 +141,7 @@ int main() {
             cAj = lean_cG(Aj, d);
         }
         Ideal mu = G;
+        int64_t wmu = cY;  // mu = G
         int64_t cycles = 0, walked = 0;
         int status = -1, hitok = 0;
         // verify: absolute position (steps from a_0, not reduced mod l) of the
@@ -150,13 +152,13 @@ int main() {
             Ideal nx;
             int64_t Qm = 0;
             const bool first = cycles == 0 && ej > 0;
-            if (!bsgs_giant((int)compose, mu, first ? Aj : Y, first ? cAj : cY, d, s, L, nx, Qm)) {
+            if (!bsgs_giant((int)compose, mu, wmu, first ? Aj : Y, first ? cAj : cY, d, s, L, nx, Qm)) {
                 status = -2;
                 break;
             }
             if (first) {  // G' = reduce(a_jl * a_j') is the stride from now on
                 Y = nx;
-                cY = lean_cG(Y, d);
+                cY = -Qm / 2;  // (b^2 - d)/(4a) = -Q_{-1}/2
             }
             St v{nx.b, 2 * nx.a, Qm};
             if (verify) {
@@ -218,6 +220,7 @@ int main() {
                 }
             }
             mu = Ideal{v.Q / 2, v.P, gc};
+            wmu = -v.Qp / 2;
         }
         std::printf("%d %d %lld %lld %lld %d %lld %d\n", status, g, (long long)baby, (long long)cycles,
                     (long long)walked, (int)tab.size(), (long long)jl, hitok);

@@ -1,10 +1,11 @@
 // Host driver for the giant-step ideal arithmetic (eis_infra.cuh), used by
 // test_infra_host.py.  Reads lines "d a1 b1 g1 a2 b2 g2" (two ideals
 // [a, (b + sqrt d)/2] with generator classes g in Z/3) and prints, for the
-// textbook composition, for NUCOMP/NUDUPL/NUCOMPchoose and for the search's
-// lean product (fp32 Euclid, the second ideal's c precomputed), whether the
+// textbook composition, for NUCOMP/NUDUPL/NUCOMPchoose, for the search's
+// lean textbook product (fp32 Euclid, the second ideal's c precomputed) and
+// for its lean NUCOMP (fp32 Euclid runs, both c's passed in), whether the
 // reduced product was formed and its (a, b, g):
-//   okT aT bT gT okN aN bN gN okL aL bL gL
+//   okT aT bT gT okN aN bN gN okL aL bL gL okM aM bM gM
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -31,9 +32,14 @@ int main() {
         bool okL = eis::lean_mul(X, Y, eis::lean_cG(Y, d), d, s, Le, Qm);
         // Q_{-1} of the result must be (d - P^2) / Q
         okL = okL && Qm * 2 * Le.a == d - Le.b * Le.b;
-        std::printf("%d %lld %lld %d %d %lld %lld %d %d %lld %lld %d\n", okT ? 1 : 0, (long long)T.a,
-                    (long long)T.b, T.g, okN ? 1 : 0, (long long)N.a, (long long)N.b, N.g, okL ? 1 : 0,
-                    (long long)Le.a, (long long)Le.b, Le.g);
+        eis::Ideal M{0, 0, 0};
+        int64_t Qm2 = 0;
+        bool okM = eis::lean_nucomp(X, eis::lean_cG(X, d), Y, eis::lean_cG(Y, d), d, s, L, M, Qm2);
+        okM = okM && Qm2 * 2 * M.a == d - M.b * M.b;
+        std::printf("%d %lld %lld %d %d %lld %lld %d %d %lld %lld %d %d %lld %lld %d\n", okT ? 1 : 0,
+                    (long long)T.a, (long long)T.b, T.g, okN ? 1 : 0, (long long)N.a, (long long)N.b, N.g,
+                    okL ? 1 : 0, (long long)Le.a, (long long)Le.b, Le.g, okM ? 1 : 0, (long long)M.a,
+                    (long long)M.b, M.g);
         std::fflush(stdout);  // one answer per line, for interactive use
     }
     return 0;

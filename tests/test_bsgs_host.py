@@ -76,7 +76,7 @@ def _check(orc, rows, out, want_verified):
 
 
 @pytest.mark.parametrize("wide", [1, 0], ids=["wide_stride", "stride_a_jl"])
-@pytest.mark.parametrize("compose", [0, 1, 2], ids=["lean", "nucomp", "textbook"])
+@pytest.mark.parametrize("compose", [0, 1, 2, 3], ids=["lean", "lean_nucomp", "textbook", "nucomp"])
 def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose, wide):
     """d up to 1e10 (whole periods walkable): every hit at l - j or l + j,
     with the stride a_jl and with the wide stride reduce(a_jl a_j')."""
@@ -91,7 +91,7 @@ def test_hits_lie_in_the_first_period_window(bsgs_host, orc, compose, wide):
     assert _check(orc, rows, out, True) > len(rows) // 2
 
 
-@pytest.mark.parametrize("compose", [0, 1, 2], ids=["lean", "nucomp", "textbook"])
+@pytest.mark.parametrize("compose", [0, 1, 2, 3], ids=["lean", "lean_nucomp", "textbook", "nucomp"])
 def test_search_matches_oracle_near_1e11_1e12_and_2p44(bsgs_host, orc, compose):
     rng = np.random.default_rng(83 + compose)
     rows = []
