@@ -36,6 +36,7 @@
 // (j <= jl) in the first period.  Hence the first hit is at l - j or l + j.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -189,24 +190,34 @@ EIS_HD float fdivmod1(float x, float y, float &rem) {
     return q;
 }
 
-// Extended Euclid on 0 <= A < 2^22, 0 < B < 2^22 in fp32: returns g = gcd(A, B)
-// with xa A + xb B = g.
+// Extended Euclid on 0 <= A < 2^22, 0 <= B < 2^22 in fp32: returns g = gcd(A, B)
+// with xa A + xb B = g.  Unrolled by two so that the pairs (r0, r1),
+// (a0, a1), (b0, b1) take turns as dividend and divisor in place; every
+// remainder, quotient and cofactor is an integer below 2^22, so each
+// operation is exact.  Invariant: a0 A + b0 B = r0, a1 A + b1 B = r1.
 EIS_HD float fegcd(float A, float B, float &xa, float &xb) {
     float r0 = A, r1 = B, a0 = 1.0f, a1 = 0.0f, b0 = 0.0f, b1 = 1.0f;
-    while (r1 != 0.0f) {
+    for (;;) {
+        if (r1 == 0.0f) {
+            xa = a0;
+            xb = b0;
+            return r0;
+        }
         float rem;
-        const float q = fdivmod1(r0, r1, rem);
-        r0 = r1;
+        float q = fdivmod1(r0, r1, rem);
+        r0 = rem;
+        a0 -= q * a1;  // |q a1| <= B: exact
+        b0 -= q * b1;
+        if (r0 == 0.0f) {
+            xa = a1;
+            xb = b1;
+            return r1;
+        }
+        q = fdivmod1(r1, r0, rem);
         r1 = rem;
-        const float ta = a0 - q * a1, tb = b0 - q * b1;  // |cofactors| <= B, A: exact
-        a0 = a1;
-        a1 = ta;
-        b0 = b1;
-        b1 = tb;
+        a1 -= q * a0;
+        b1 -= q * b0;
     }
-    xa = a0;
-    xb = b0;
-    return r0;
 }
 
 // x mod m in [0, m) for |x| < 2^23, 0 < m < 2^23.
