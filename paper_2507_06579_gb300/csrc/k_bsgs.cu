@@ -128,45 +128,31 @@ __device__ __forceinline__ void walk_record_body(
         uint32_t n = 0, back = 0;
         bool hit = false, full = false;
         for (;;) {
+            // ws[i] is position done + n + i + 2 (state 1 had 0 steps); a marked
+            // state is stored as it is reached, with S = acc_i + steps_i (mod 3,
+            // reduced by the reader)
+            const uint32_t st0 = done + n + 1;
             LeanState ws[kRecGroup];
-            ws[0] = w;
-            const bool c0 = lean_step<kFast>(ws[0], C);
-            bool any = c0;
-            bool mark = ws[0].Q < T;
+            bool any = false, c0 = false;
+            int a = w.acc;
 #pragma unroll
-            for (int i = 1; i < kRecGroup; ++i) {
-                ws[i] = ws[i - 1];
-                any |= lean_step<kFast>(ws[i], C);
-                mark |= ws[i].Q < T;
-            }
-            const uint32_t n0 = n;  // steps of this invocation before the group
-            n += kRecGroup;
-            int sum = 0;
-#pragma unroll
-            for (int i = 0; i < kRecGroup; ++i) sum += ws[i].x;
-            const int acc0 = w.acc;
-            const int acc = w.acc + sum;
-            w = ws[kRecGroup - 1];
-            w.acc = acc;
-            mark &= rec_on;
-            if (__any_sync(kFull, mark)) {
-                if (mark) {
-                    // ws[i] is position done + n0 + i + 2 (state 1 had 0 steps);
-                    // S = acc_i + steps_i (mod 3), reduced by the reader
-                    int a = acc0;
-                    const uint32_t st0 = done + n0 + 1;
-#pragma unroll
-                    for (int i = 0; i < kRecGroup; ++i) {
-                        a += ws[i].x;
-                        if (ws[i].Q < T && k < (uint32_t)kBsgsKmax) {
-                            jl = st0 + (uint32_t)i + 1;
-                            store_entry(tab + k, ws[i].Q, ws[i].num, (uint32_t)a + st0 + (uint32_t)i, jl);
-                            ++k;
-                        }
-                    }
-                    full = k >= (uint32_t)kBsgsKmax;
+            for (int i = 0; i < kRecGroup; ++i) {
+                ws[i] = i ? ws[i - 1] : w;
+                const bool ci = lean_step<kFast>(ws[i], C);
+                if (i == 0) c0 = ci;
+                any |= ci;
+                a += ws[i].x;
+                if (rec_on && ws[i].Q < T && k < (uint32_t)kBsgsKmax) {
+                    jl = st0 + (uint32_t)i + 1;
+                    store_entry(tab + k, ws[i].Q, ws[i].num, (uint32_t)a + st0 + (uint32_t)i, jl);
+                    ++k;
                 }
             }
+            n += kRecGroup;
+            const int acc = a;
+            w = ws[kRecGroup - 1];
+            w.acc = acc;
+            full = k >= (uint32_t)kBsgsKmax;
             if (__any_sync(kFull, any)) {
                 hit = any;
                 int post = 0;
@@ -254,9 +240,6 @@ namespace {
 
 // Steps per warp vote while the lanes walk to their marked states.
 constexpr int kBsgsGroup = 4;
-// A refill also brings into L2 the table of the record this many positions
-// further on, which some lane will take shortly.
-constexpr uint32_t kPrefetchAhead = 8192;
 
 __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, uint32_t fb_cap,
                                          uint32_t cand, int *status) {
@@ -326,7 +309,7 @@ __device__ __forceinline__ void bsgs_body(
     uint32_t *fp_warp = fp_all + (threadIdx.x & ~31u) * kFpWords;  // lane t's words at t * kFpWords
     uint32_t *fp_mine = fp_warp + lane * kFpWords;
     bool active = false, exhausted = false;
-    uint32_t cand = 0, cycles = 0, k = 0, region_ahead = 0xffffffffu;
+    uint32_t cand = 0, cycles = 0, k = 0;
     int64_t d = 0, s = 0, L = 0;
     float T = 0.0f, C = 0.0f;
     const uint4 *tab = nullptr;
@@ -359,8 +342,6 @@ __device__ __forceinline__ void bsgs_body(
             if (!active) {
                 const uint32_t idx = base + __popc(need & lt);
                 if (idx < n) {
-                    region_ahead = idx + kPrefetchAhead < n ? recs[idx + kPrefetchAhead].region
-                                                            : 0xffffffffu;
                     const uint4 r0 = *reinterpret_cast<const uint4 *>(recs + idx);  // cand, k, region, s
                     cand = r0.x;
                     k = r0.y;
@@ -388,12 +369,6 @@ __device__ __forceinline__ void bsgs_body(
             }
             sl[lane] = 0u;
             sl[lane + 32] = 0u;
-            // 16 lanes bring the table kPrefetchAhead records on into L2
-            const uint32_t ra = __shfl_sync(kFull, region_ahead, src);
-            if (ra != 0xffffffffu && lane < (int)(kBsgsRegionBytes / 128)) {
-                const unsigned char *pa = pool + (size_t)ra * kBsgsRegionBytes + 128 * lane;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-            }
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < kBsgsKmax / 32; ++t)
