@@ -48,6 +48,7 @@ __device__ __forceinline__ void store_entry(DEntry *e, float Q, float num, uint3
 }
 
 constexpr int kRecGroup = 10;  // steps per warp vote in the recording walk
+constexpr uint32_t kRecEpoch = 256;  // least steps between hand-offs of a warp's lanes
 
 // The recording baby walk.  Queue positions [q_lo, min(q_hi, n_surv)) are
 // taken from the end of the survivor queue (largest d first), as in the
@@ -122,9 +123,17 @@ __device__ __forceinline__ void walk_record_body(
             }
         }
         if (!__any_sync(kFull, active)) break;
-        const uint32_t cap = (active && rec_on) ? min(nbaby, step_limit) : step_limit;
-        uint32_t room = active ? cap - min(done, cap) : 0xffffffffu;
-        for (int o = 16; o > 0; o >>= 1) room = min(room, __shfl_xor_sync(kFull, room, o));
+        // Steps before the warp next stops to hand d on or refill: at least
+        // kRecEpoch, so that lanes hand on together (a lane past nbaby keeps
+        // recording: a longer table only lengthens the stride), but never past
+        // a lane's step limit.
+        uint32_t rem_rec = (active && rec_on) ? nbaby - min(done, nbaby) : 0xffffffffu;
+        uint32_t rem_lim = active ? step_limit - min(done, step_limit) : 0xffffffffu;
+        for (int o = 16; o > 0; o >>= 1) {
+            rem_rec = min(rem_rec, __shfl_xor_sync(kFull, rem_rec, o));
+            rem_lim = min(rem_lim, __shfl_xor_sync(kFull, rem_lim, o));
+        }
+        const uint32_t room = min(max(rem_rec, kRecEpoch), rem_lim);
         uint32_t n = 0, back = 0;
         bool hit = false, full = false;
         for (;;) {
