@@ -144,6 +144,10 @@ __device__ __forceinline__ void walk_record_body(
             LeanState ws[kRecGroup];
             bool any = false, c0 = false;
             int a = w.acc;
+            // a group records only while the table has room for all its steps,
+            // so each step needs a single compare; a table that cannot take a
+            // whole group is full (every marked state up to jl is in it)
+            const bool rec_g = rec_on && k + (uint32_t)kRecGroup <= (uint32_t)kBsgsKmax;
 #pragma unroll
             for (int i = 0; i < kRecGroup; ++i) {
                 ws[i] = i ? ws[i - 1] : w;
@@ -151,7 +155,7 @@ __device__ __forceinline__ void walk_record_body(
                 if (i == 0) c0 = ci;
                 any |= ci;
                 a += ws[i].x;
-                if (rec_on && ws[i].Q < T && k < (uint32_t)kBsgsKmax) {
+                if (rec_g && ws[i].Q < T) {
                     jl = st0 + (uint32_t)i + 1;
                     store_entry(tab + k, ws[i].Q, ws[i].num, (uint32_t)a + st0 + (uint32_t)i, jl);
                     ++k;
@@ -161,7 +165,7 @@ __device__ __forceinline__ void walk_record_body(
             const int acc = a;
             w = ws[kRecGroup - 1];
             w.acc = acc;
-            full = k >= (uint32_t)kBsgsKmax;
+            full = rec_on && k + (uint32_t)kRecGroup > (uint32_t)kBsgsKmax;
             if (__any_sync(kFull, any)) {
                 hit = any;
                 int post = 0;
