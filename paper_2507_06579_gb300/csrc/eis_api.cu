@@ -1001,8 +1001,9 @@ int eis_get_tune_table(eis_ctx *c, eis_tune_row *rows, size_t cap, size_t *n_out
 // Candidate (nbaby, mark_every) pairs of the decade tuner; {0, 16} is the
 // walk alone.
 static const eis_tune_row kTuneGrid[] = {
-    {0, 0, 16},     {0, 1024, 16}, {0, 2048, 16}, {0, 2048, 32},
-    {0, 3072, 32},  {0, 4096, 32}, {0, 6144, 64}, {0, 8192, 64},
+    {0, 0, 16},    {0, 1024, 16}, {0, 1536, 24}, {0, 2048, 24}, {0, 2048, 32},
+    {0, 2048, 40}, {0, 2304, 48}, {0, 2560, 32}, {0, 3072, 32}, {0, 3072, 40},
+    {0, 4096, 32}, {0, 4096, 48}, {0, 6144, 64}, {0, 8192, 64},
 };
 
 int eis_autotune_decades(eis_ctx *c, uint64_t d_lo, uint64_t d_hi, eis_tune_row *rows_out,
