@@ -44,6 +44,7 @@ struct eis_ctx {
     uint32_t *d_primes = nullptr;
     uint64_t *d_sqtab = nullptr;  // per odd prime p: (p^2)^(-1) mod 2^64, floor((2^64-1)/p^2)
     uint32_t nprimes = 0;
+    std::vector<uint32_t> primes;  // host copy of the odd primes of d_primes
     int *d_single = nullptr;  // [0] result, [1] steps, [2] status
     unsigned char *d_query = nullptr;  // K3 single query: u64 d, i8 out, int status, u64 acc[2], u32 next
     int mode = EIS_MODE_PERSISTENT;
@@ -709,6 +710,7 @@ int eis_create(eis_ctx **out, int device, uint64_t mem_budget_bytes) {
     }
     std::vector<uint32_t> pr = odd_primes_below(1u << 22);
     c->nprimes = (uint32_t)pr.size();
+    c->primes = pr;
     // Every table of the context is charged once: primes, the square-free
     // test table (16 B per prime), the single-query words.
     if (!ctx_reserve(c, pr.size() * 4 + pr.size() * 16 + 4 * sizeof(int) + 64)) {
@@ -1292,7 +1294,19 @@ int eis_is_eisenstein(eis_ctx *c, uint64_t d, int *result_out) {
     unsigned char *q = c->d_query;  // [0] d, [8] out, [12] status, [16] acc[2], [32] next, [40] flag
     uint32_t *sq_flag = reinterpret_cast<uint32_t *>(q + 40);
     EIS_CK(cudaMemsetAsync(q, 0, 64, c->stream));
-    k_sqfree_one<<<c->sm_count * 2, 256, 0, c->stream>>>(d, c->d_sqtab, c->nprimes, sq_flag);
+    {
+        // only odd primes with p^2 <= d can divide d: scan those, on as many
+        // blocks as they fill (at most two per SM)
+        uint64_t r = (uint64_t)std::sqrt((double)d);
+        while (r * r > d) --r;
+        while ((r + 1) * (r + 1) <= d) ++r;
+        const uint32_t np = (uint32_t)(std::upper_bound(c->primes.begin(), c->primes.end(),
+                                                        (uint32_t)std::min<uint64_t>(r, UINT32_MAX)) -
+                                       c->primes.begin());
+        const uint32_t blocks = std::max<uint32_t>(1u, std::min<uint32_t>((np + 255) / 256,
+                                                                          (uint32_t)c->sm_count * 2));
+        k_sqfree_one<<<blocks, 256, 0, c->stream>>>(d, c->d_sqtab, np, sq_flag);
+    }
     EIS_CK(cudaGetLastError());
     if (c->mode == EIS_MODE_PLAIN) {
         // one lane walks the half period

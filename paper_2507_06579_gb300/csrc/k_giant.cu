@@ -227,7 +227,7 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
 //   ds == nullptr : item i is candidate cands[i] of the Seg layout (already
 //                   square-free); its flag bit / log byte are written.
 // Dynamic shared memory: (blockDim.x / 32) tables of 2^log2n uint64.
-__global__ void __launch_bounds__(128) k_giant(const uint64_t *__restrict__ ds,
+__global__ void __launch_bounds__(32) k_giant(const uint64_t *__restrict__ ds,
                                                const Seg *__restrict__ segs, uint32_t nseg,
                                                const uint32_t *__restrict__ cands,
                                                const uint32_t *__restrict__ n_ptr, uint32_t n_fixed,

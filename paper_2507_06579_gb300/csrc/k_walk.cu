@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(256, 4) k_walk_persistent(
 #undef EIS_WALK_BODY
 }
 
-// Square-free test of one d by a whole grid: *flag |= 1 when p^2 | d for an
-// odd prime p of the table.  A prime with p^2 > d cannot divide d (d > 0)
-// and the divisibility test is exact for any d, so the whole table is
-// scanned with no bound (d < 2^44 needs p < 2^22, the table's range).
+// Square-free test of one d by a grid: *flag |= 1 when p^2 | d for one of
+// the first nprimes odd primes of the table.  The caller passes the primes
+// with p^2 <= d (no larger prime can divide d; d < 2^44 needs p < 2^22, the
+// table's range) and sizes the grid to them.
 __global__ void __launch_bounds__(256) k_sqfree_one(uint64_t d, const uint64_t *__restrict__ sqtab,
                                                     uint32_t nprimes, uint32_t *__restrict__ flag) {
     bool hit = false;

@@ -8,6 +8,8 @@ the oracle, plus the paper's Table 1 total inside it and a Moebius count of D.
 """
 import concurrent.futures as cf
 
+import math
+
 import numpy as np
 import pytest
 
@@ -56,6 +58,33 @@ def test_known_points(ctx):
     with pytest.raises(E.EisError) as ei:
         ctx.is_eisenstein(E.EIS_D_LIMIT + 5)
     assert ei.value.code == E.EIS_ERANGE
+
+
+def test_membership_square_factor_at_the_scan_bound(ctx, orc):
+    """A single query scans only the odd primes p with p^2 <= d: d = 5 p^2 with
+    p the largest prime below a bound (the last prime the scan needs, at
+    several sizes, up to 2^44) is refused as not square-free; d = 5 p^2 + 8,
+    square-free or not, matches the oracle."""
+    def prevprime(n):
+        n -= 1
+        while any(n % q == 0 for q in range(2, math.isqrt(n) + 1)):
+            n -= 1
+        return n
+
+    for bound in (7, 1000, 10**5, math.isqrt(E.EIS_D_LIMIT // 5)):
+        p = prevprime(bound)
+        d = 5 * p * p
+        assert d % 8 == 5 and d < E.EIS_D_LIMIT
+        with pytest.raises(E.EisError) as ei:
+            ctx.is_eisenstein(d)
+        assert ei.value.code == E.EIS_ENOTD, d
+        d2 = d + 8
+        rc, theta, _ = orc.walk_mod2(d2)
+        if rc == orc.ORC_ENOTD:
+            with pytest.raises(E.EisError):
+                ctx.is_eisenstein(d2)
+        else:
+            assert ctx.is_eisenstein(d2) == (theta == 1), d2
 
 
 def test_is_eisenstein_matches_oracle(ctx, orc):
