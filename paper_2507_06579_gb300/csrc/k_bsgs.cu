@@ -307,6 +307,10 @@ __device__ __forceinline__ bool fp_maybe(const uint32_t *sl, uint32_t q, uint32_
     return true;
 }
 
+struct SIdeal {
+    int32_t a, b, g;
+};
+
 template <bool kFast, int kCompose>
 __device__ __forceinline__ void bsgs_body(
     const Seg *__restrict__ segs, uint32_t nseg, const DRecord *__restrict__ recs,
@@ -323,14 +327,17 @@ __device__ __forceinline__ void bsgs_body(
     uint32_t *fp_mine = fp_warp + lane * kFpWords;
     bool active = false, exhausted = false;
     uint32_t cand = 0, cycles = 0, k = 0;
-    int64_t d = 0, s = 0, L = 0;
+    int64_t d = 0;
+    int32_t s = 0, L = 0;  // floor(sqrt d) < 2^22 and its square root
     float T = 0.0f, C = 0.0f;
     const uint4 *tab = nullptr;
     // G = a_jl starts the search; the stride Y is reduce(a_jl * a_j') (taken
     // by the first cycle from Y = a_j', `first`), or a_jl when no table state
     // lies kBsgsWideGap steps before jl
-    Ideal G{1, 1, 0}, mu{1, 1, 0}, Y{1, 1, 0};
-    int64_t wY = 0, wmu = 0;  // third form coefficients (b^2 - d)/(4a) of Y and mu
+    // reduced ideals of the lane's d, every coefficient below 2^22: held in
+    // 32 bits and widened for the product
+    SIdeal G{1, 1, 0}, mu{1, 1, 0}, Y{1, 1, 0};
+    int32_t wY = 0, wmu = 0;  // third form coefficients (b^2 - d)/(4a) of Y and mu
     bool first = false;
     // the lane's walk, carried across iterations: it composes when its last
     // walk has ended (compose_now), else walks on
@@ -341,7 +348,7 @@ __device__ __forceinline__ void bsgs_body(
     bool at_x = false, compose_now = false;
     float numx = 0.0f;
     uint32_t walked = 0;
-    unsigned long long my_cycles = 0, my_walk = 0;
+    uint32_t my_cycles = 0, my_walk = 0;
     for (;;) {
         // ---- refill idle lanes from the records
         const unsigned need = __ballot_sync(kFull, !active);
@@ -359,7 +366,7 @@ __device__ __forceinline__ void bsgs_body(
                     cand = r0.x;
                     k = r0.y;
                     tab = reinterpret_cast<const uint4 *>(pool + (size_t)r0.z * kBsgsRegionBytes);
-                    s = (int64_t)r0.w;
+                    s = (int32_t)r0.w;
                     fresh = true;
                 }
             }
@@ -425,13 +432,13 @@ __device__ __forceinline__ void bsgs_body(
             jy = __shfl_sync(kFull, jy, ej & 31);
             jz = __shfl_sync(kFull, jz, ej & 31);
             if (lane == src) {
-                G.a = (int64_t)__uint_as_float(gx) / 2;
-                G.b = (int64_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
+                G.a = (int32_t)__uint_as_float(gx) / 2;
+                G.b = (int32_t)__uint_as_float(gy) - s;  // floor(P + s (+ 1/2)) - s = P
                 G.g = (int)(gz % 3u);
                 first = ej > 0;
                 if (first) {
-                    Y.a = (int64_t)__uint_as_float(jx) / 2;
-                    Y.b = (int64_t)__uint_as_float(jy) - s;
+                    Y.a = (int32_t)__uint_as_float(jx) / 2;
+                    Y.b = (int32_t)__uint_as_float(jy) - s;
                     Y.g = (int)(jz % 3u);
                 } else {
                     Y = G;
@@ -442,10 +449,10 @@ __device__ __forceinline__ void bsgs_body(
         if (fresh) {
             d = (int64_t)cand_to_d(segs, nseg, cand);
             if (kCompose == 1) {
-                L = (int64_t)isqrt44((uint64_t)s);
-                wmu = lean_cG(G, d);
+                L = (int32_t)isqrt44((uint64_t)s);
+                wmu = (int32_t)lean_cG(Ideal{G.a, G.b, G.g}, d);
             }
-            wY = lean_cG(Y, d);
+            wY = (int32_t)lean_cG(Ideal{Y.a, Y.b, Y.g}, d);
             C = __uint2float_rn((uint32_t)(kFast ? 2 * s + 1 : 2 * s));
             Cw = C;
             T = __fmul_rn(tt.tau[tune_row(tt, (uint64_t)d)], __uint2float_rn((uint32_t)s));
@@ -460,7 +467,9 @@ __device__ __forceinline__ void bsgs_body(
         if (active && compose_now) {
             Ideal nx{1, 1, 0};
             int64_t Qm = 2;
-            const bool ok = bsgs_giant(kCompose, mu, wmu, Y, wY, d, s, L, nx, Qm) && ++cycles <= max_cycles;
+            const bool ok = bsgs_giant(kCompose, Ideal{mu.a, mu.b, mu.g}, wmu, Ideal{Y.a, Y.b, Y.g}, wY, d,
+                                       s, L, nx, Qm) &&
+                            ++cycles <= max_cycles;
             if (!ok) {
                 fallback(fb_list, fb_count, fb_cap, cand, status);
                 my_cycles += cycles;
@@ -468,8 +477,8 @@ __device__ __forceinline__ void bsgs_body(
             } else {
                 if (first) {  // the first landing, reduce(a_jl * a_j'), is the stride
                     first = false;
-                    Y = nx;
-                    wY = -Qm / 2;  // (b^2 - d)/(4a) = -Q_{-1}/2
+                    Y = SIdeal{(int32_t)nx.a, (int32_t)nx.b, nx.g};
+                    wY = (int32_t)(-Qm / 2);  // (b^2 - d)/(4a) = -Q_{-1}/2
                 }
                 w.num = bsgs_num(nx.b, s, kFast);
                 w.Q = __uint2float_rn((uint32_t)(2 * nx.a));
@@ -567,10 +576,10 @@ __device__ __forceinline__ void bsgs_body(
             my_cycles += cycles;
             active = false;
         } else {  // the next giant step starts from x + 1
-            mu.a = (int64_t)w.Q / 2;
-            mu.b = (int64_t)w.num - s;
+            mu.a = (int32_t)w.Q / 2;
+            mu.b = (int32_t)w.num - s;
             mu.g = gc % 3;
-            wmu = -(int64_t)w.Qp / 2;  // Q_{-1} of x + 1 is Q_x
+            wmu = -(int32_t)w.Qp / 2;  // Q_{-1} of x + 1 is Q_x
         }
     }
     warp_add(&acc[0], my_walk);
