@@ -87,7 +87,7 @@ extern "C" {
 #define EIS_OPT_MARK_EVERY 12    /* lane search: about 1 state in this many is */
                                  /* marked and kept in the baby table (16)     */
 #define EIS_OPT_BSGS_CHUNK 13    /* lane search: survivors per round of record */
-                                 /* walk + search (2^22); sizes the table pool */
+                                 /* walk + search (2^23); sizes the table pool */
 #define EIS_OPT_BSGS_WALK_CAP 14 /* lane search: steps a giant cycle may walk  */
                                  /* without meeting a marked state before its  */
                                  /* d is finished by the plain walk (2^14)     */

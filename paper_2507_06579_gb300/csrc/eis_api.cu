@@ -57,7 +57,7 @@ struct eis_ctx {
     int giant_compose = EIS_COMPOSE_TEXTBOOK;
     int giant_kernel = EIS_GIANT_LANE;
     int mark_every = 16;                    // marked states: about 1 in mark_every
-    int64_t bsgs_chunk = (int64_t)1 << 22;  // survivors per record/search round
+    int64_t bsgs_chunk = (int64_t)1 << 23;  // survivors per record/search round
     int64_t bsgs_walk_cap = 1 << 14;        // steps a giant cycle's walk may take
     int64_t bsgs_window = 64;               // steps a lane walks per search iteration (0: no limit)
     int occ_persistent = 1;
@@ -1120,7 +1120,7 @@ int eis_autotune(eis_ctx *c, uint64_t lo, uint64_t hi, eis_tune_result *out) {
     const int64_t lane_thr = c->giant_kernel == EIS_GIANT_LANE && c->giant_threshold > 0
                                  ? c->giant_threshold
                                  : 2048;
-    for (int64_t chunk : {(int64_t)1 << 21, (int64_t)1 << 22, (int64_t)1 << 23})
+    for (int64_t chunk : {(int64_t)1 << 22, (int64_t)1 << 23, (int64_t)1 << 24, (int64_t)1 << 25})
         cands.push_back({occ, EIS_GIANT_LANE, lane_thr, chunk});
     const Setting prev{c->ctas_per_sm, c->giant_kernel, c->giant_threshold, c->bsgs_chunk};
     const int prev_mode = c->mode;
