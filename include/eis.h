@@ -81,7 +81,10 @@ extern "C" {
 #define EIS_OPT_MEM_BUDGET 9     /* read-only: the context's device-memory    */
                                  /* budget in bytes                           */
 #define EIS_OPT_MEM_IN_USE 10    /* read-only: bytes charged to the budget    */
-                                 /* (context tables, live plans and servers)  */
+                                 /* (context tables, live plans and servers,  */
+                                 /* and the lane-search table pool a freed    */
+                                 /* plan leaves for the next; a plan that     */
+                                 /* needs the room reclaims it)               */
 #define EIS_OPT_GIANT_KERNEL 11  /* which search takes walks past the          */
                                  /* threshold: EIS_GIANT_* (EIS_GIANT_LANE)    */
 #define EIS_OPT_MARK_EVERY 12    /* lane search: about 1 state in this many is */

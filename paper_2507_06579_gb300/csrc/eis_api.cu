@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -47,6 +48,12 @@ struct eis_ctx {
     std::vector<uint32_t> primes;  // host copy of the odd primes of d_primes
     int *d_single = nullptr;  // [0] result, [1] steps, [2] status
     unsigned char *d_query = nullptr;  // K3 single query: u64 d, i8 out, int status, u64 acc[2], u32 next
+    // A lane-search table pool kept from a freed plan for the next one (its
+    // bytes stay charged to in_use): freeing and mapping tens of GB per plan
+    // cost milliseconds in every eis_classify_range / eis_count_range call.
+    std::mutex pool_mu;
+    unsigned char *pool_cache = nullptr;
+    uint64_t pool_cache_bytes = 0;
     int mode = EIS_MODE_PERSISTENT;
     int ctas_per_sm = 0;
     int threads = 256;
@@ -107,6 +114,7 @@ struct eis_plan {
     TuneTab tt{};  // the settings each d looks up
     DRecord *d_recs = nullptr;
     unsigned char *d_pool = nullptr;
+    uint64_t pool_bytes = 0;  // size of d_pool (possibly a larger cached pool)
     uint32_t *d_fb = nullptr;
     uint32_t *d_bctr = nullptr;  // [0] walk head [1] records [3] search head
                                  // [4] fallbacks [5] fallback walk head
@@ -149,6 +157,48 @@ static int plan_alloc(eis_plan *p, void **ptr, size_t bytes) {
     }
     p->bytes += bytes;
     return EIS_OK;
+}
+
+// The cached search pool if it holds at least `bytes` (its charge moves to the
+// caller, *got = its size); a smaller one is freed.  nullptr if none fits.
+static unsigned char *pool_take(eis_ctx *c, uint64_t bytes, uint64_t *got) {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    *got = 0;
+    if (!c->pool_cache) return nullptr;
+    unsigned char *q = c->pool_cache;
+    const uint64_t qb = c->pool_cache_bytes;
+    c->pool_cache = nullptr;
+    c->pool_cache_bytes = 0;
+    if (qb >= bytes) {
+        *got = qb;
+        return q;
+    }
+    cudaFree(q);
+    ctx_release(c, qb);
+    return nullptr;
+}
+
+// Keep a freed plan's pool (still charged) for the next plan; of two pools
+// the larger is kept.  The caller has synchronized the device, so no kernel
+// still uses it.
+static void pool_give(eis_ctx *c, unsigned char *q, uint64_t bytes) {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    if (c->pool_cache && c->pool_cache_bytes >= bytes) {
+        cudaFree(q);
+        ctx_release(c, bytes);
+        return;
+    }
+    if (c->pool_cache) {
+        cudaFree(c->pool_cache);
+        ctx_release(c, c->pool_cache_bytes);
+    }
+    c->pool_cache = q;
+    c->pool_cache_bytes = bytes;
+}
+
+static uint64_t pool_cached_bytes(eis_ctx *c) {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    return c->pool_cache_bytes;
 }
 
 static uint64_t num_candidates(uint64_t lo, uint64_t hi, uint64_t *d0) {
@@ -313,6 +363,14 @@ static void plan_free(eis_plan *p) {
         if (e) cudaEventDestroy(e);
     for (auto &e : p->bev)
         if (e) cudaEventDestroy(e);
+    if (p->d_pool && p->ctx) {
+        // the pool goes to the context's cache; wait for any kernel still
+        // using it (as cudaFree would)
+        cudaDeviceSynchronize();
+        pool_give(p->ctx, p->d_pool, p->pool_bytes);
+        p->bytes -= std::min(p->bytes, p->pool_bytes);
+        p->d_pool = nullptr;
+    }
     void *bufs[] = {p->d_segs, p->d_tiles, p->d_sqfree, p->d_flags, p->d_tile_pop, p->d_tile_off,
                     p->d_surv, p->d_ctr, p->d_status, p->d_counts, p->d_steps, p->d_glog,
                     p->d_defer, p->d_cls, p->d_recs, p->d_pool, p->d_fb, p->d_bctr};
@@ -428,7 +486,8 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
         const uint64_t lanes = (uint64_t)c->sm_count * c->occ_record * 256;
         const uint64_t per_d = kBsgsRegionBytes + sizeof(DRecord) + 4;
         const uint64_t used = c->in_use.load();
-        const uint64_t left = c->budget > used ? c->budget - used : 0;
+        const uint64_t cached = pool_cached_bytes(c);  // reclaimable
+        const uint64_t left = c->budget + cached > used ? c->budget + cached - used : 0;
         const uint64_t fit = left / per_d > lanes + 64 ? left / per_d - lanes - 64 : 0;
         uint64_t C = std::min<uint64_t>((uint64_t)c->bsgs_chunk, (p->total_cand + 31) / 32 * 32);
         C = std::min<uint64_t>(C, fit / 32 * 32);
@@ -440,7 +499,16 @@ static int plan_build(eis_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t
             p->bsgs_rounds = (uint32_t)((p->total_cand + C - 1) / C);
             p->bsgs_grid_a = (uint32_t)(c->sm_count * c->occ_record);
             p->bsgs_grid_b = (uint32_t)(c->sm_count * c->occ_bsgs);
-            EIS_ALLOC(p->d_pool, (lanes + C) * kBsgsRegionBytes);
+            const uint64_t pool_need = (lanes + C) * kBsgsRegionBytes;
+            uint64_t got = 0;
+            p->d_pool = pool_take(c, pool_need, &got);
+            if (p->d_pool) {
+                p->pool_bytes = got;  // its charge moves to this plan
+                p->bytes += got;
+            } else {
+                EIS_ALLOC(p->d_pool, pool_need);
+                p->pool_bytes = pool_need;
+            }
             EIS_ALLOC(p->d_recs, C * sizeof(DRecord));
             EIS_ALLOC(p->d_fb, C * 4);
             EIS_ALLOC(p->d_bctr, 8 * sizeof(uint32_t));
@@ -778,6 +846,7 @@ int eis_destroy(eis_ctx *c) {
     if (c->d_single) cudaFree(c->d_single);
     if (c->d_query) cudaFree(c->d_query);
     if (c->d_sqtab) cudaFree(c->d_sqtab);
+    if (c->pool_cache) cudaFree(c->pool_cache);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return EIS_OK;
