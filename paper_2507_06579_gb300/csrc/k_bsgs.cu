@@ -3,11 +3,13 @@
 //
 //  k_walk_record  the persistent baby walk (k_walk.cu's lean step, ten steps
 //                 per warp vote, work stealing from the survivor queue) that
-//                 also records every marked state into the lane's table
-//                 region.  A d whose centre does not come within nbaby steps
-//                 (or whose table fills) is handed on as a DRecord, and the
-//                 lane takes the region that belongs to that record's slot
-//                 for its next d.
+//                 also stores every marked state, as the step reaches it,
+//                 into the lane's table region.  A d whose centre does not
+//                 come within nbaby steps (or whose table fills) is handed on
+//                 as a DRecord; a warp stops to hand on and refill at most
+//                 every kRecEpoch steps, so a lane may record a little past
+//                 nbaby.  The lane then takes the region that belongs to that
+//                 record's slot for its next d.
 //  k_bsgs_t       one d per lane, lanes refilled from the records (the warp
 //                 loads a fresh lane's table coalesced and indexes it as
 //                 fingerprints in that lane's shared memory): each cycle
@@ -15,9 +17,10 @@
 //                 first marked state x and one step beyond, and looks x up
 //                 under its direct and mirror keys (shared-memory probes; a
 //                 fingerprint match is settled by a warp-wide exact scan of
-//                 the entries); the next cycle composes from state x + 1.  A d the search cannot finish
-//                 (reduction or walk past its limits) goes to a fallback
-//                 list that the plain persistent walk finishes.
+//                 the entries); the next cycle composes from state x + 1.
+//                 A d the search cannot finish (reduction or walk past its
+//                 limits) goes to a fallback list that the plain persistent
+//                 walk finishes.
 #include "eis.h"
 #include "eis_bsgs.cuh"
 #include "eis_common.cuh"

@@ -142,3 +142,33 @@ def test_batched_intervals_with_the_search(ctx):
         p.destroy()
     assert np.array_equal(c0, c1)
     assert st["deferred"] > 0
+
+
+def test_pool_kept_for_the_next_plan_and_never_shared(ctx):
+    """A freed plan's table pool goes to the context and the next plan takes
+    it; two live plans never share one.  Plans built while another lives,
+    launched on two streams at once, give the count of a plan alone, and the
+    bytes in use come back to where they were (context tables and one kept
+    pool)."""
+    import torch
+    lo, hi = 10**10, 10**10 + 8 * ((1 << 19) + 3)
+    with _opts(ctx, giant_threshold=1024, mark_every=16, giant_kernel=E.EIS_GIANT_LANE):
+        ref = ctx.count_range(lo, hi)
+        used0 = ctx.get_option(E.EIS_OPT_MEM_IN_USE)
+        a = ctx.plan_create([lo], [hi])
+        b = ctx.plan_create([lo], [hi])
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        a.launch(s1)
+        b.launch(s2)
+        torch.cuda.synchronize()
+        assert int(a.counts()[0]) == ref and int(b.counts()[0]) == ref
+        assert a.stats()["deferred"] > 0
+        a.destroy()
+        c = ctx.plan_create([lo], [hi])  # takes a's pool
+        c.launch(s1)
+        b.launch(s2)
+        torch.cuda.synchronize()
+        assert int(c.counts()[0]) == ref and int(b.counts()[0]) == ref
+        b.destroy()
+        c.destroy()
+        assert ctx.get_option(E.EIS_OPT_MEM_IN_USE) == used0
