@@ -422,6 +422,8 @@ def main():
     if args.serve_seconds > 0 and rank == 0:
         from paper_2507_06579_gb300 import workloads as W
         rates = []
+        checked = mismatches = 0
+        vrng = np.random.default_rng(9)
         with E.Server(ctx) as srv:
             for rate in SERVE_RATES:
                 # at least 1000 requests per rate (300 at 10 req/s, 30 s of
@@ -435,6 +437,21 @@ def main():
                                  [r[2] for r in reqs], [r[3] for r in reqs])
                 lat = out["latency_us"] / 1e3
                 ok = (out["status"] == E.EIS_OK) | (out["status"] == E.EIS_ENOTD)
+                # a sample of the answers (outside the replay's clock) against
+                # the context's own count_range / is_eisenstein, which the
+                # parity tests pin to the oracle
+                for i in vrng.choice(n, size=min(n, 40), replace=False):
+                    _, kind, rlo, rhi = reqs[i]
+                    if kind == "member":
+                        try:
+                            want, wst = int(ctx.is_eisenstein(rlo)), E.EIS_OK
+                        except E.EisError as ex:
+                            want, wst = 0, ex.code
+                        good = out["status"][i] == wst and (wst != E.EIS_OK or int(out["results"][i]) == want)
+                    else:
+                        good = out["status"][i] == E.EIS_OK and int(out["results"][i]) == ctx.count_range(rlo, rhi)
+                    checked += 1
+                    mismatches += 0 if good else 1
                 rates.append({"rate_rps": rate, "requests": n, "ok": int(ok.sum()),
                               "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99)),
@@ -444,6 +461,7 @@ def main():
         # saturation: the first offered rate the server no longer keeps up with
         # (throughput below 95% of the offered rate); its throughput is the
         # server's capacity on this mix
+        assert mismatches == 0, "server answers differ from count_range / is_eisenstein"
         sat = next((r for r in rates if r["throughput_rps"] < 0.95 * r["rate_rps"]), None)
         serving = {"workload": "Poisson arrivals, 90% counts [a, a+L) with a log-uniform in "
                                "[1e6, 1e12], L log-uniform in [1e2, 1e6]; 10% membership "
@@ -458,6 +476,8 @@ def main():
                                   {"offered_rps": None,
                                    "note": "kept up with every offered rate up to %g req/s"
                                            % rates[-1]["rate_rps"]}),
+                   "verified": {"checked": checked, "mismatches": mismatches,
+                                "against": "eis_count_range / eis_is_eisenstein of the same context"},
                    "batches": sst["batches"], "deferred": sst["deferred"],
                    "max_batch_parts": sst["max_batch_parts"]}
 
