@@ -194,6 +194,9 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
     }
     uint32_t giants = 6;  // compositions on a lane's way to its first giant step
     if (!__all_sync(kFull, ok)) return res;
+    // the stride is fixed from here on: the textbook composition takes the
+    // search's lean product (fp32 Euclid, c of the stride computed once)
+    const int64_t cS = compose ? 0 : lean_cG(stride, dd);
     for (uint32_t r = 0; r < max_rounds; ++r) {
         const uint64_t e = infra_find(tab, log2n, infra_key(2 * mu.a, mu.b));
         const unsigned hit = __ballot_sync(kFull, e != 0);
@@ -209,7 +212,8 @@ __device__ GiantOut giant_one(uint64_t d, uint64_t *tab, int log2n, int nbaby, u
             return res;
         }
         Ideal t;
-        ok = giant_mul(compose, mu, stride, dd, s, L, t);
+        int64_t Qm;
+        ok = compose ? giant_mul(compose, mu, stride, dd, s, L, t) : lean_mul(mu, stride, cS, dd, s, t, Qm);
         mu = t;
         if (!__all_sync(kFull, ok)) return res;
         giants += 32;
