@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256, 3) k_walk_record(
 namespace {
 
 // Steps per warp vote while the lanes walk to their marked states.
-constexpr int kBsgsGroup = 4;
+constexpr int kBsgsGroup = 2;
 
 __device__ __forceinline__ void fallback(uint32_t *fb_list, uint32_t *fb_count, uint32_t fb_cap,
                                          uint32_t cand, int *status) {
