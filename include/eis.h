@@ -249,7 +249,7 @@ int eis_get_tune_table(eis_ctx *ctx, eis_tune_row *rows, size_t cap, size_t *n_o
 
 /* For every decade [10^k, 10^(k+1)) that meets [d_lo, d_hi): time the walk
  * alone and the lane search at a grid of (nbaby, mark_every) on the top
- * 2^21 candidates of the decade inside [d_lo, d_hi), and keep the fastest
+ * 2^22 candidates of the decade inside [d_lo, d_hi), and keep the fastest
  * (the walk unless a setting is 2% faster; every setting must give the same
  * count).  The rows found replace those of the installed table for the same
  * decades (the table keeps at most EIS_TUNE_MAX_ROWS rows, merging equal

@@ -1094,7 +1094,7 @@ int eis_autotune_decades(eis_ctx *c, uint64_t d_lo, uint64_t d_hi, eis_tune_row 
         const uint64_t top = std::min(dec_hi, d_hi);
         const uint64_t bot = std::max(dec_lo, d_lo);
         if (bot >= top) continue;
-        const uint64_t width = (uint64_t)8 << 21;  // 2^21 candidates
+        const uint64_t width = (uint64_t)8 << 22;  // 2^22 candidates
         const uint64_t slo = top - bot > width ? top - width : bot;
         uint64_t ref = 0;
         double best_ms = 1e300, walk_ms = 1e300;
